@@ -1,0 +1,189 @@
+/*
+ * cgks.h -- C ABI of the GB300 (sm_103a) library for one two-stage
+ * fourth-order (S2O4) time step of the compact gas-kinetic scheme with
+ * adaptive stencil extension and discontinuity feedback factor (ASE-DFF-CGKS)
+ * on structured 1-D / 2-D Cartesian meshes.
+ *
+ * Method (paper sections, equations and algorithms):
+ *   S2O4 stepping of cell averages and gradients ........ Sec. 2.2, Eq. 2.13-2.30
+ *   gas-kinetic flux and interface state ................. Sec. 2.1, Eq. 2.6-2.8, 2.11-2.12
+ *   discontinuity feedback factor (DFF) .................. Sec. 3.1, Eq. 3.1-3.5
+ *   ASE-DFF Hermite reconstruction (r5/r7/r9, HWENO-AO) .. Sec. 3.2, Eq. 3.6-3.19, Algorithm 1
+ *   2-D dimension-by-dimension reconstruction (Steps 1-4)  Sec. 3.3
+ *   collision time and CFL time step ..................... Sec. 4 (opening paragraphs)
+ *
+ * Conventions
+ *   - Every call returns 0 (CGKS_OK) or a negative CGKS_E* code; nothing throws.
+ *   - Host arrays are FP64, structure of arrays, C order:
+ *       W, Wx, Wy            [nvar][ny][nx]     nvar = 3 (1-D: rho, rho U, rho E)
+ *                                                    = 4 (2-D: rho, rho U, rho V, rho E)
+ *       Wx_line, Wy_line     [m][nvar][ny][nx]  m = 2, 3, 4 Gauss points per face
+ *                                               for order 5, 7, 9 (2-D only)
+ *       sigma_x              [ny][nx+1]         DFF strength of x-faces (face f lies
+ *                                               between cells f-1 and f)
+ *       sigma_y              [ny+1][nx]         DFF strength of y-faces
+ *     1-D meshes use ny = 1 and pass NULL for every y array.
+ *   - Wx / Wy are cell averages of the x / y derivative; Wx_line[l] is the
+ *     x-derivative averaged along the l-th Gauss line y = y_j + xi_l dy of the
+ *     cell (Sec. 3.3, "line averaged slopes").
+ *   - The library owns the solver and all device memory.  A solver is not
+ *     thread safe; distinct solvers are independent.  Results are
+ *     deterministic: the same inputs give bitwise identical outputs.
+ *   - `stream` arguments are cudaStream_t values passed as void* (NULL means
+ *     the legacy default stream).
+ */
+#ifndef CGKS_H
+#define CGKS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- codes */
+#define CGKS_OK 0
+#define CGKS_EINVAL (-1)     /* invalid argument (order, size, gamma, cfl, pointer) */
+#define CGKS_ENOMEM (-2)     /* device allocation failed */
+#define CGKS_ECUDA (-3)      /* a CUDA runtime call failed */
+#define CGKS_ENONPHYS (-4)   /* non-positive density / pressure or non-finite value */
+#define CGKS_ETIMEOUT (-5)   /* a bounded device wait gave up */
+#define CGKS_ENOTSUP (-6)    /* combination of options not supported */
+
+/* precision of the reconstruction and kinetic arithmetic */
+#define CGKS_FP64 0          /* everything in FP64 */
+#define CGKS_FP32_BULK 1     /* reconstruction / kinetics in FP32; cell averages,
+                                their accumulation, DFF and positivity tests in FP64 */
+/* collision time (Sec. 4) */
+#define CGKS_TAU_ZERO 0      /* tau = 0 (smooth inviscid tests, Sec. 4.6) */
+#define CGKS_TAU_HGKS 1      /* tau = c1 dt + c2 |pl - pr| / (pl + pr) dt */
+/* boundary conditions, per side: bc[0..3] = x-low, x-high, y-low, y-high */
+#define CGKS_BC_PERIODIC 0
+#define CGKS_BC_TRANSMISSIVE 1  /* ghost = nearest interior cell, normal slopes zero */
+#define CGKS_BC_FIXED 2         /* 1-D only: ghost cells fixed by cgks_set_ghost */
+
+typedef struct {
+    int dim;            /* 1 or 2 */
+    int order;          /* 5, 7 or 9: ASE-DFF(5,3), (7,5,3), (9,7,5,3) */
+    int precision;      /* CGKS_FP64 or CGKS_FP32_BULK */
+    int tau_mode;       /* CGKS_TAU_ZERO or CGKS_TAU_HGKS */
+    int bc[4];          /* CGKS_BC_* per side */
+    double gamma;       /* ratio of specific heats, > 1 */
+    double cfl;         /* CFL number of the time-step rule, > 0 */
+    double sigma_thres; /* DFF threshold, Eq. 3.3 (1.0 for compact stencils) */
+    double gamma_hi;    /* HWENO-AO linear weight of the big stencil, Eq. 3.12 (0.85) */
+    double gamma_lo;    /* HWENO-AO low-order split, Eq. 3.12 (0.6) */
+    double weno_eps;    /* epsilon of the WENO-Z weights, Eq. 3.14 (1e-8) */
+    double tau_c1;      /* c1 of the HGKS collision time (0.05) */
+    double tau_c2;      /* c2 of the HGKS collision time (1.0) */
+} cgks_params;
+
+typedef struct cgks_solver cgks_solver;
+typedef struct cgks_batch cgks_batch;
+
+typedef struct {
+    double t;            /* simulated time */
+    long long steps;     /* completed steps */
+    double min_rho, min_p;
+    double mass[4];      /* sum over cells of W * dx * dy, per variable */
+    long long branch[4]; /* normal-reconstruction branches (per cell and Gauss
+                            line, both directions) of the latest step's two
+                            stages: HWENO-AO, linear r5, r7, r9 (batches: summed) */
+} cgks_stats;
+
+/* Fill *p with the paper's defaults for (dim, order): gamma 1.4, CFL 0.5,
+ * sigma_thres 1, gamma_hi 0.85, gamma_lo 0.6, eps 1e-8, c1 0.05, c2 1,
+ * FP64, tau = 0, periodic.  Returns CGKS_EINVAL for a NULL p. */
+int cgks_default_params(cgks_params* p, int dim, int order);
+
+/* Create a solver for an nx x ny mesh on [x0,x1] x [y0,y1] (1-D: ny = 1,
+ * y bounds ignored).  All device buffers are allocated here on `stream`'s
+ * device; the CUDA graph of one step is captured on first use.
+ * Errors: CGKS_EINVAL (NULL out/p, dim not 1/2, order not 5/7/9, nx or ny < 1,
+ * ny != 1 in 1-D, gamma <= 1, cfl <= 0, non-positive extent, FIXED bc in 2-D),
+ * CGKS_ENOMEM, CGKS_ECUDA.  On error *out is NULL. */
+int cgks_init_mesh(cgks_solver** out, const cgks_params* p, int nx, int ny,
+                   double x0, double x1, double y0, double y1, void* stream);
+
+/* Copy a host state in (synchronous).  sigma_x / sigma_y may be NULL: sigma is
+ * then initialised from Eq. 3.2 applied to the two cell averages adjacent to
+ * each face.  Returns CGKS_ENONPHYS if some cell has rho <= 0 or p <= 0,
+ * CGKS_EINVAL for a NULL required array. */
+int cgks_set_state(cgks_solver* s, const double* W, const double* Wx, const double* Wy,
+                   const double* Wx_line, const double* Wy_line,
+                   const double* sigma_x, const double* sigma_y);
+
+/* As cgks_set_state, with device pointers (same layouts), enqueued on the
+ * solver's stream.  sigma pointers may be NULL (initialised on the device). */
+int cgks_set_state_device(cgks_solver* s, const double* W, const double* Wx, const double* Wy,
+                          const double* Wx_line, const double* Wy_line,
+                          const double* sigma_x, const double* sigma_y);
+
+/* 1-D, CGKS_BC_FIXED sides: ghost cells [2 sides][3 layers][2 fields W,Wx][3 vars]
+ * (layer 0 touches the boundary).  Host pointer; copied. */
+int cgks_set_ghost(cgks_solver* s, const double* ghost);
+
+/* Time step of the CFL rule: dt = cfl * min over cells of min(dx,dy) / (|U| + a),
+ * a = sqrt(gamma p / rho).  Synchronous. */
+int cgks_compute_dt(cgks_solver* s, double* dt);
+
+/* Enqueue one S2O4 step (two stages) on the solver's stream as one CUDA graph
+ * launch.  dt > 0: use it; dt <= 0: use the CFL rule, evaluated on the device
+ * (no host round trip).  Returns only host-detectable errors; device status
+ * (non-physical states) is reported by cgks_sync. */
+int cgks_step(cgks_solver* s, double dt);
+
+/* Enqueue n steps of fixed dt (> 0) or CFL steps (dt <= 0). */
+int cgks_advance(cgks_solver* s, int n, double dt);
+
+/* Wait for the solver's stream.  t_out (may be NULL) receives the simulated
+ * time; bad_cell (may be NULL) the first cell index flagged.  Returns
+ * CGKS_ENONPHYS if any stage met rho <= 0, p <= 0 or a non-finite value. */
+int cgks_sync(cgks_solver* s, double* t_out, long long* bad_cell);
+
+/* Copy the state out (synchronous), FP64 whatever the precision.  Any output
+ * pointer may be NULL to skip that array. */
+int cgks_get_state(cgks_solver* s, double* W, double* Wx, double* Wy, double* Wx_line,
+                   double* Wy_line, double* sigma_x, double* sigma_y);
+
+/* Device-pointer variant of cgks_get_state, enqueued on the solver's stream. */
+int cgks_get_state_device(cgks_solver* s, double* W, double* Wx, double* Wy, double* Wx_line,
+                          double* Wy_line, double* sigma_x, double* sigma_y);
+
+/* Diagnostics (synchronous). */
+int cgks_get_stats(cgks_solver* s, cgks_stats* st);
+
+/* Number of graph nodes (kernel launches) one CFL step makes. */
+int cgks_step_info(cgks_solver* s, int* kernels_per_step);
+
+void cgks_destroy(cgks_solver* s);
+const char* cgks_strerror(int code);
+
+/* ---------------------------------------------------------------- batch
+ * Many independent 2-D meshes advanced together: every kernel of a stage is
+ * one persistent launch over a device work list of all instances, and the
+ * two-stage step is one CUDA graph.  Instance k has nx[k] x ny[k] cells on
+ * [ext[4k], ext[4k+1]] x [ext[4k+2], ext[4k+3]]; all share *p.  States are
+ * concatenated per instance in the single-mesh layouts above. */
+int cgks_batch_init(cgks_batch** out, const cgks_params* p, int n, const int* nx, const int* ny,
+                    const double* ext, void* stream);
+int cgks_batch_set_state(cgks_batch* b, int k, const double* W, const double* Wx, const double* Wy,
+                         const double* Wx_line, const double* Wy_line);
+/* one step of all instances; dt[k] > 0 fixed per instance, or NULL: each
+ * instance takes its own CFL dt on the device. */
+int cgks_batch_step(cgks_batch* b, const double* dt);
+int cgks_batch_sync(cgks_batch* b);
+int cgks_batch_get_state(cgks_batch* b, int k, double* W, double* Wx, double* Wy,
+                         double* Wx_line, double* Wy_line);
+void cgks_batch_destroy(cgks_batch* b);
+
+/* ---------------------------------------------------------------- host tables
+ * The reconstruction functionals the kernels use, for inspection (no GPU
+ * needed).  Stencil st: 0 S0, 1 S1, 2 S2, 3 r5, 4 r7, 5 r9 (Sec. 3.2); row:
+ * 0..2 value, d/dxi, d2/dxi2 at xi = +1/2; 3..5 the same at xi = -1/2;
+ * 6..9 values at the m Gauss nodes of `order`.  out[10] multiplies
+ * [Qbar_{i-2..i+2}, dx*Qx_{i-2..i+2}]. */
+int cgks_stencil_row(int order, int st, int row, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,683 @@
+// Host side of the C ABI declared in include/cgks.h.
+//
+// A single-mesh solver is a batch of one: every kernel is a grid-stride loop
+// over the work items of all meshes of a descriptor table (see
+// cgks_kernels.cuh), launched with one persistent grid sized to the GPU
+// (SM count x resident blocks).  One S2O4 step (Sec. 2.2) is captured once as
+// a CUDA graph:
+//   [CFL reduction] -> dt -> stage 1 (lines, normal, flux, update)
+//                         -> stage 2 (lines, normal, flux, update)
+// Device memory of all meshes lives in one slab allocated at init.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/cgks.h"
+#include "cgks_kernels.cuh"
+#include "kfns.h"
+#include "tables.h"
+
+using namespace cgks;
+
+namespace {
+
+int g_tables_device = -1;  // device whose constant tables are loaded
+
+int load_tables()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CGKS_ECUDA;
+    if (g_tables_device == dev) return CGKS_OK;
+    CgksTables t[3];
+    TabF f[3];
+    for (int k = 0; k < 3; ++k) {
+        if (cgks_build_tables(5 + 2 * k, &t[k]) != 0) return CGKS_EINVAL;
+        for (int a = 0; a < 6; ++a)
+            for (int b = 0; b < 10; ++b)
+                for (int c = 0; c < 10; ++c) f[k].row[a][b][c] = (float)t[k].row[a][b][c];
+        for (int a = 0; a < 4; ++a)
+            for (int b = 0; b < 5; ++b)
+                for (int c = 0; c < 10; ++c) f[k].cpoly[a][b][c] = (float)t[k].cpoly[a][b][c];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) f[k].bm2[a][b] = (float)t[k].bm2[a][b];
+        for (int a = 0; a < 5; ++a)
+            for (int b = 0; b < 5; ++b) f[k].bm4[a][b] = (float)t[k].bm4[a][b];
+        for (int a = 0; a < 4; ++a) {
+            f[k].gx[a] = (float)t[k].gx[a];
+            f[k].gw[a] = (float)t[k].gw[a];
+            for (int b = 0; b < 12; ++b) { f[k].d1[a][b] = (float)t[k].d1[a][b]; f[k].d2[a][b] = (float)t[k].d2[a][b]; }
+        }
+    }
+    Kfns all[8] = {kfns_1_1_d(), kfns_1_1_f(), kfns_2_2_d(), kfns_2_3_d(), kfns_2_4_d(),
+                   kfns_2_2_f(), kfns_2_3_f(), kfns_2_4_f()};
+    for (int q = 0; q < 8; ++q)
+        if (all[q].upload(t, f) != 0) return CGKS_ECUDA;
+    g_tables_device = dev;
+    return CGKS_OK;
+}
+
+Kfns pick_kfns(int dim, int order, int prec)
+{
+    int M = (order - 1) / 2;
+    if (dim == 1) return prec == CGKS_FP64 ? kfns_1_1_d() : kfns_1_1_f();
+    if (prec == CGKS_FP64) return M == 2 ? kfns_2_2_d() : (M == 3 ? kfns_2_3_d() : kfns_2_4_d());
+    return M == 2 ? kfns_2_2_f() : (M == 3 ? kfns_2_3_f() : kfns_2_4_f());
+}
+
+enum { W_LINES = 0, W_NORMAL, W_FLUX, W_CELLS, W_SIGINIT, W_COUNT };
+
+} // namespace
+
+struct cgks_batch {
+    cgks_params p;
+    int n = 0, dim = 2, M = 1, nvar = 4, nplanes = 0, nacc = 0;
+    size_t rsize = 8;
+    cudaStream_t stream = nullptr;
+    std::vector<Mesh> host;      // host copy of the descriptors
+    Mesh* dmesh = nullptr;       // device descriptors
+    long long* doff = nullptr;   // device prefix arrays [W_COUNT][n+1]
+    std::vector<long long> off;  // host prefix arrays
+    double* dfixed = nullptr;    // fixed dt per mesh
+    char* slab = nullptr;
+    Kfns k;
+    int grid[16];
+    int nsm = 0;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // [0] fixed dt, [1] CFL dt
+    int kernels_per_step = 0;
+    bool state_set = false;
+    bool own_stream = false;
+};
+
+struct cgks_solver {
+    cgks_batch* b = nullptr;
+};
+
+namespace {
+
+#define CK(x)                                                   \
+    do {                                                        \
+        cudaError_t e_ = (x);                                   \
+        if (e_ != cudaSuccess) return e_ == cudaErrorMemoryAllocation ? CGKS_ENOMEM : CGKS_ECUDA; \
+    } while (0)
+
+Work work_of(const cgks_batch* b, int kind)
+{
+    Work w;
+    w.mesh = b->dmesh;
+    w.off = b->doff + (size_t)kind * (b->n + 1);
+    w.n = b->n;
+    w.total = b->off[(size_t)kind * (b->n + 1) + b->n];
+    return w;
+}
+
+long long items(int kind, int dim, int M, int nx, int ny)
+{
+    switch (kind) {
+    case W_LINES: return dim == 2 ? (long long)(nx + 6) * (ny + 2) + (long long)(ny + 6) * (nx + 2) : 0;
+    case W_NORMAL: return dim == 2 ? 2LL * (nx + 2) * (ny + 2) * M : nx + 2;
+    case W_FLUX: return dim == 2 ? ((long long)(nx + 1) * ny + (long long)(ny + 1) * nx) * M : nx + 1;
+    case W_CELLS: return (long long)nx * ny;
+    default: return dim == 2 ? (long long)(nx + 1) * ny + (long long)(ny + 1) * nx : nx + 1;
+    }
+}
+
+int launch(cgks_batch* b, const void* fn, int kind, int gi, int stage, bool has_stage)
+{
+    Work w = work_of(b, kind);
+    if (w.total == 0) return CGKS_OK;
+    int threads = (kind == W_FLUX) ? 128 : 256;
+    long long need = (w.total + threads - 1) / threads;
+    int grid = (int)std::min<long long>(need, (long long)b->grid[gi]);
+    if (grid < 1) grid = 1;
+    void* args2[] = {&w, &stage};
+    void* args1[] = {&w};
+    CK(cudaLaunchKernel(fn, dim3(grid), dim3(threads), has_stage ? args2 : args1, 0, b->stream));
+    return CGKS_OK;
+}
+
+int enqueue_stage(cgks_batch* b, int stage)
+{
+    int r;
+    if (b->dim == 2 && (r = launch(b, (const void*)b->k.lines, W_LINES, 0, stage, true))) return r;
+    if ((r = launch(b, (const void*)b->k.normal, W_NORMAL, 1, stage, true))) return r;
+    if ((r = launch(b, (const void*)(stage == 1 ? b->k.flux1 : b->k.flux2), W_FLUX, stage == 1 ? 2 : 3, 0, false))) return r;
+    if ((r = launch(b, (const void*)(stage == 1 ? b->k.upd1 : b->k.upd2), W_CELLS, stage == 1 ? 4 : 5, 0, false))) return r;
+    return CGKS_OK;
+}
+
+int enqueue_step(cgks_batch* b, bool cfl)
+{
+    int r;
+    if (cfl && (r = launch(b, (const void*)b->k.cfl, W_CELLS, 6, 0, false))) return r;
+    int use = cfl ? 1 : 0;
+    const double* fx = b->dfixed;
+    Mesh* dm = b->dmesh;
+    int n = b->n;
+    void* args[] = {&dm, &n, &use, &fx};
+    CK(cudaLaunchKernel((const void*)k_dt<0>, dim3((n + 127) / 128), dim3(128), args, 0, b->stream));
+    if ((r = enqueue_stage(b, 1))) return r;
+    if ((r = enqueue_stage(b, 2))) return r;
+    return CGKS_OK;
+}
+
+int build_graph(cgks_batch* b, int which)
+{
+    if (b->gexec[which]) return CGKS_OK;
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int r = enqueue_step(b, which == 1);
+    cudaGraph_t gg = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->stream, &gg);
+    if (r) { if (gg) cudaGraphDestroy(gg); return r; }
+    if (e != cudaSuccess) return CGKS_ECUDA;
+    g = gg;
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    b->kernels_per_step = (int)nn;
+    e = cudaGraphInstantiate(&b->gexec[which], g, 0);
+    cudaGraphDestroy(g);
+    return e == cudaSuccess ? CGKS_OK : CGKS_ECUDA;
+}
+
+int validate(const cgks_params* p)
+{
+    if (!p) return CGKS_EINVAL;
+    if (p->dim != 1 && p->dim != 2) return CGKS_EINVAL;
+    if (p->order != 5 && p->order != 7 && p->order != 9) return CGKS_EINVAL;
+    if (p->precision != CGKS_FP64 && p->precision != CGKS_FP32_BULK) return CGKS_EINVAL;
+    if (p->tau_mode != CGKS_TAU_ZERO && p->tau_mode != CGKS_TAU_HGKS) return CGKS_EINVAL;
+    if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->sigma_thres > 0.0)) return CGKS_EINVAL;
+    if (!(p->gamma_hi > 0.0 && p->gamma_hi < 1.0) || !(p->gamma_lo > 0.0 && p->gamma_lo < 1.0)) return CGKS_EINVAL;
+    if (!(p->weno_eps > 0.0)) return CGKS_EINVAL;
+    for (int s = 0; s < 4; ++s) {
+        if (p->bc[s] < 0 || p->bc[s] > 2) return CGKS_EINVAL;
+        if (p->bc[s] == CGKS_BC_FIXED && (p->dim == 2 || s >= 2)) return CGKS_EINVAL;
+    }
+    return CGKS_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// per-mesh slab layout
+struct Layout {
+    size_t S, ACC, sigx, sigy, LA[2], FR[2], FO[2], SP[2], scal, total;
+};
+
+Layout layout(int dim, int M, size_t rs, int nx, int ny)
+{
+    Layout L;
+    size_t plane = (size_t)nx * ny;
+    int np = dim == 2 ? 12 + 8 * M : 6;
+    int nacc = dim == 2 ? 4 + 8 * M : 6;
+    size_t o = 0;
+    L.S = o; o = align256(o + 2 * np * plane * 8);
+    L.ACC = o; o = align256(o + nacc * plane * 8);
+    L.sigx = o; o = align256(o + 2 * (size_t)(nx + 1) * ny * 8);
+    L.sigy = o; o = align256(o + (dim == 2 ? 2 * (size_t)(ny + 1) * nx * 8 : 0));
+    for (int d = 0; d < 2; ++d) {
+        int na = d == 0 ? nx : ny, nb = d == 0 ? ny : nx;
+        bool on = dim == 2 || d == 0;
+        L.LA[d] = o; o = align256(o + (on && dim == 2 ? (size_t)(nb + 2) * (na + 6) * M * 4 * rs : 0));
+        L.FR[d] = o; o = align256(o + (on ? (size_t)(nb + 2) * (na + 1) * M * 24 * rs : 0));
+        L.FO[d] = o; o = align256(o + (on ? (size_t)nb * (na + 1) * M * 16 * rs : 0));
+        L.SP[d] = o; o = align256(o + (on ? (size_t)nb * (na + 1) * M * 8 : 0));
+    }
+    L.scal = o; o = align256(o + 512);
+    L.total = o;
+    return L;
+}
+
+int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, const int* ny,
+                 const double* ext, void* stream)
+{
+    if (!out) return CGKS_EINVAL;
+    *out = nullptr;
+    int r = validate(p);
+    if (r) return r;
+    if (n < 1 || !nx || !ny || !ext) return CGKS_EINVAL;
+    for (int k = 0; k < n; ++k) {
+        if (nx[k] < 1 || ny[k] < 1 || (p->dim == 1 && ny[k] != 1)) return CGKS_EINVAL;
+        if (!(ext[4 * k + 1] > ext[4 * k]) || (p->dim == 2 && !(ext[4 * k + 3] > ext[4 * k + 2]))) return CGKS_EINVAL;
+    }
+    if ((r = load_tables())) return r;
+    cgks_batch* b = new (std::nothrow) cgks_batch();
+    if (!b) return CGKS_ENOMEM;
+    b->p = *p;
+    b->n = n;
+    b->dim = p->dim;
+    b->M = p->dim == 2 ? (p->order - 1) / 2 : 1;
+    b->nvar = p->dim + 2;
+    b->nplanes = p->dim == 2 ? 12 + 8 * b->M : 6;
+    b->nacc = p->dim == 2 ? 4 + 8 * b->M : 6;
+    b->rsize = p->precision == CGKS_FP64 ? 8 : 4;
+    b->stream = (cudaStream_t)stream;
+    if (!b->stream) {
+        // graph capture needs a non-legacy stream: own one
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return CGKS_ECUDA; }
+        b->own_stream = true;
+    }
+    b->k = pick_kfns(p->dim, p->order, p->precision);
+    std::vector<Layout> L(n);
+    size_t total = 0;
+    std::vector<size_t> base(n);
+    for (int k = 0; k < n; ++k) {
+        L[k] = layout(p->dim, b->M, b->rsize, nx[k], ny[k]);
+        base[k] = total;
+        total += L[k].total;
+    }
+    total = align256(total + n * sizeof(double));
+    cudaError_t e = cudaMalloc(&b->slab, total);
+    if (e != cudaSuccess) { delete b; return e == cudaErrorMemoryAllocation ? CGKS_ENOMEM : CGKS_ECUDA; }
+    b->dfixed = (double*)(b->slab + total - align256(n * sizeof(double)));
+    b->host.resize(n);
+    double K = p->dim == 2 ? (4.0 - 2.0 * p->gamma) / (p->gamma - 1.0) : (3.0 - p->gamma) / (p->gamma - 1.0);
+    for (int k = 0; k < n; ++k) {
+        Mesh& g = b->host[k];
+        std::memset(&g, 0, sizeof(g));
+        g.nx = nx[k]; g.ny = ny[k]; g.order = p->order; g.oi = (p->order - 5) / 2;
+        for (int s = 0; s < 4; ++s) g.bc[s] = p->bc[s];
+        g.tau_mode = p->tau_mode;
+        g.dx = (ext[4 * k + 1] - ext[4 * k]) / nx[k];
+        g.dy = p->dim == 2 ? (ext[4 * k + 3] - ext[4 * k + 2]) / ny[k] : 1.0;
+        g.gamma = p->gamma; g.K = K; g.thr = p->sigma_thres; g.ghi = p->gamma_hi; g.glo = p->gamma_lo;
+        g.eps = p->weno_eps; g.c1 = p->tau_c1; g.c2 = p->tau_c2; g.cfl = p->cfl;
+        g.plane = (long long)nx[k] * ny[k];
+        char* m0 = b->slab + base[k];
+        g.S0 = (double*)(m0 + L[k].S);
+        g.S1 = g.S0 + (size_t)b->nplanes * g.plane;
+        g.ACC = (double*)(m0 + L[k].ACC);
+        g.sig_x = (double*)(m0 + L[k].sigx);
+        g.sig_xn = g.sig_x + (size_t)(nx[k] + 1) * ny[k];
+        g.sig_y = p->dim == 2 ? (double*)(m0 + L[k].sigy) : nullptr;
+        g.sig_yn = p->dim == 2 ? g.sig_y + (size_t)(ny[k] + 1) * nx[k] : nullptr;
+        for (int d = 0; d < 2; ++d) {
+            g.LA[d] = m0 + L[k].LA[d];
+            g.FR[d] = m0 + L[k].FR[d];
+            g.FO[d] = m0 + L[k].FO[d];
+            g.SP[d] = (double*)(m0 + L[k].SP[d]);
+        }
+        char* sc = m0 + L[k].scal;
+        g.dt = (double*)sc;
+        g.t = (double*)(sc + 8);
+        g.status = (unsigned*)(sc + 16);
+        g.bad = (long long*)(sc + 24);
+        g.smax = (unsigned long long*)(sc + 32);
+        g.branch = (unsigned long long*)(sc + 40);
+        g.ghost = (const double*)(sc + 80);  // 36 doubles of fixed ghost cells (1-D)
+    }
+    // prefix arrays
+    b->off.assign((size_t)W_COUNT * (n + 1), 0);
+    for (int kind = 0; kind < W_COUNT; ++kind)
+        for (int k = 0; k < n; ++k)
+            b->off[(size_t)kind * (n + 1) + k + 1] = b->off[(size_t)kind * (n + 1) + k] + items(kind, p->dim, b->M, nx[k], ny[k]);
+    int rr = CGKS_OK;
+    do {
+        if (cudaMalloc(&b->dmesh, n * sizeof(Mesh)) != cudaSuccess) { rr = CGKS_ENOMEM; break; }
+        if (cudaMalloc(&b->doff, b->off.size() * sizeof(long long)) != cudaSuccess) { rr = CGKS_ENOMEM; break; }
+        if (cudaMemcpy(b->dmesh, b->host.data(), n * sizeof(Mesh), cudaMemcpyHostToDevice) != cudaSuccess) { rr = CGKS_ECUDA; break; }
+        if (cudaMemcpy(b->doff, b->off.data(), b->off.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess) { rr = CGKS_ECUDA; break; }
+        // zero the scalars and scratch once (bad index = max)
+        if (cudaMemsetAsync(b->slab, 0, total, b->stream) != cudaSuccess) { rr = CGKS_ECUDA; break; }
+        for (int k = 0; k < n; ++k) {
+            long long mx = LLONG_MAX;
+            if (cudaMemcpyAsync(b->host[k].bad, &mx, 8, cudaMemcpyHostToDevice, b->stream) != cudaSuccess) { rr = CGKS_ECUDA; break; }
+        }
+        if (cudaStreamSynchronize(b->stream) != cudaSuccess) { rr = CGKS_ECUDA; break; }
+        // persistent grids: SM count x resident blocks of each kernel
+        int dev;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
+        const void* fns[7] = {(const void*)b->k.lines, (const void*)b->k.normal, (const void*)b->k.flux1,
+                              (const void*)b->k.flux2, (const void*)b->k.upd1, (const void*)b->k.upd2,
+                              (const void*)b->k.cfl};
+        for (int q = 0; q < 7; ++q) {
+            int occ = 1;
+            if (fns[q]) {
+                int th = (q == 2 || q == 3) ? 128 : 256;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fns[q], th, 0) != cudaSuccess) occ = 1;
+            }
+            b->grid[q] = std::max(1, occ) * b->nsm;
+        }
+    } while (0);
+    if (rr) { cgks_batch_destroy(b); return rr; }
+    *out = b;
+    return CGKS_OK;
+}
+
+int status_of(cgks_batch* b, long long* bad_out)
+{
+    int rc = CGKS_OK;
+    long long first = LLONG_MAX;
+    for (int k = 0; k < b->n; ++k) {
+        unsigned st = 0;
+        long long bad = LLONG_MAX;
+        CK(cudaMemcpy(&st, b->host[k].status, 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&bad, b->host[k].bad, 8, cudaMemcpyDeviceToHost));
+        if (st & STATUS_NONPHYS) { rc = CGKS_ENONPHYS; first = std::min(first, bad); }
+    }
+    if (bad_out) *bad_out = rc ? first : -1;
+    return rc;
+}
+
+int set_state_impl(cgks_batch* b, int k, const double* W, const double* Wx, const double* Wy,
+                   const double* Wxl, const double* Wyl, const double* sx, const double* sy,
+                   cudaMemcpyKind kind, bool sync)
+{
+    if (k < 0 || k >= b->n) return CGKS_EINVAL;
+    Mesh& g = b->host[k];
+    size_t P = (size_t)g.plane;
+    int nv = b->nvar;
+    if (!W || !Wx) return CGKS_EINVAL;
+    if (b->dim == 2 && (!Wy || !Wxl || !Wyl)) return CGKS_EINVAL;
+    cudaStream_t s = b->stream;
+    CK(cudaMemcpyAsync(g.S0, W, nv * P * 8, kind, s));
+    CK(cudaMemcpyAsync(g.S0 + nv * P, Wx, nv * P * 8, kind, s));
+    if (b->dim == 2) {
+        CK(cudaMemcpyAsync(g.S0 + 8 * P, Wy, 4 * P * 8, kind, s));
+        CK(cudaMemcpyAsync(g.S0 + 12 * P, Wxl, 4 * b->M * P * 8, kind, s));
+        CK(cudaMemcpyAsync(g.S0 + (12 + 4 * b->M) * P, Wyl, 4 * b->M * P * 8, kind, s));
+    }
+    CK(cudaMemsetAsync(g.status, 0, 4, s));
+    CK(cudaMemsetAsync(g.t, 0, 8, s));
+    long long mx = LLONG_MAX;
+    CK(cudaMemcpyAsync(g.bad, &mx, 8, cudaMemcpyHostToDevice, s));
+    if (sx) {
+        CK(cudaMemcpyAsync(g.sig_x, sx, (size_t)(g.nx + 1) * g.ny * 8, kind, s));
+        if (b->dim == 2) {
+            if (!sy) return CGKS_EINVAL;
+            CK(cudaMemcpyAsync(g.sig_y, sy, (size_t)(g.ny + 1) * g.nx * 8, kind, s));
+        }
+    }
+    if (sync) CK(cudaStreamSynchronize(s));
+    return CGKS_OK;
+}
+
+// Run the per-mesh init kernels (sigma init when needed, positivity check)
+// over the whole table after a set_state.
+int post_set(cgks_batch* b, bool init_sigma)
+{
+    int r;
+    if (init_sigma && (r = launch(b, (const void*)b->k.siginit, W_SIGINIT, 6, 0, false))) return r;
+    if ((r = launch(b, (const void*)b->k.check, W_CELLS, 6, 0, false))) return r;
+    CK(cudaStreamSynchronize(b->stream));
+    return status_of(b, nullptr);
+}
+
+} // namespace
+
+extern "C" {
+
+int cgks_default_params(cgks_params* p, int dim, int order)
+{
+    if (!p) return CGKS_EINVAL;
+    std::memset(p, 0, sizeof(*p));
+    p->dim = dim;
+    p->order = order;
+    p->precision = CGKS_FP64;
+    p->tau_mode = CGKS_TAU_ZERO;
+    p->gamma = 1.4;
+    p->cfl = 0.5;
+    p->sigma_thres = 1.0;
+    p->gamma_hi = 0.85;
+    p->gamma_lo = 0.6;
+    p->weno_eps = 1e-8;
+    p->tau_c1 = 0.05;
+    p->tau_c2 = 1.0;
+    return CGKS_OK;
+}
+
+int cgks_init_mesh(cgks_solver** out, const cgks_params* p, int nx, int ny, double x0, double x1,
+                   double y0, double y1, void* stream)
+{
+    if (!out) return CGKS_EINVAL;
+    *out = nullptr;
+    double ext[4] = {x0, x1, y0, y1};
+    cgks_batch* b = nullptr;
+    int r = batch_create(&b, p, 1, &nx, &ny, ext, stream);
+    if (r) return r;
+    cgks_solver* s = new (std::nothrow) cgks_solver();
+    if (!s) { cgks_batch_destroy(b); return CGKS_ENOMEM; }
+    s->b = b;
+    *out = s;
+    return CGKS_OK;
+}
+
+int cgks_set_state(cgks_solver* s, const double* W, const double* Wx, const double* Wy, const double* Wx_line,
+                   const double* Wy_line, const double* sigma_x, const double* sigma_y)
+{
+    if (!s) return CGKS_EINVAL;
+    int r = set_state_impl(s->b, 0, W, Wx, Wy, Wx_line, Wy_line, sigma_x, sigma_y, cudaMemcpyHostToDevice, true);
+    if (r) return r;
+    s->b->state_set = true;
+    return post_set(s->b, sigma_x == nullptr);
+}
+
+int cgks_set_state_device(cgks_solver* s, const double* W, const double* Wx, const double* Wy,
+                          const double* Wx_line, const double* Wy_line, const double* sigma_x,
+                          const double* sigma_y)
+{
+    if (!s) return CGKS_EINVAL;
+    int r = set_state_impl(s->b, 0, W, Wx, Wy, Wx_line, Wy_line, sigma_x, sigma_y, cudaMemcpyDeviceToDevice, false);
+    if (r) return r;
+    s->b->state_set = true;
+    if (sigma_x == nullptr) return launch(s->b, (const void*)s->b->k.siginit, W_SIGINIT, 6, 0, false);
+    return CGKS_OK;
+}
+
+int cgks_set_ghost(cgks_solver* s, const double* ghost)
+{
+    if (!s || !ghost || s->b->dim != 1) return CGKS_EINVAL;
+    CK(cudaMemcpy((void*)s->b->host[0].ghost, ghost, 36 * sizeof(double), cudaMemcpyHostToDevice));
+    return CGKS_OK;
+}
+
+int cgks_compute_dt(cgks_solver* s, double* dt)
+{
+    if (!s || !dt) return CGKS_EINVAL;
+    cgks_batch* b = s->b;
+    int r = launch(b, (const void*)b->k.cfl, W_CELLS, 6, 0, false);
+    if (r) return r;
+    unsigned long long bits = 0, zero = 0;
+    CK(cudaMemcpyAsync(&bits, b->host[0].smax, 8, cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(b->host[0].smax, &zero, 8, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    double sm;
+    std::memcpy(&sm, &bits, 8);
+    *dt = sm > 0.0 ? b->p.cfl / sm : 0.0;
+    return CGKS_OK;
+}
+
+int cgks_step(cgks_solver* s, double dt)
+{
+    if (!s) return CGKS_EINVAL;
+    return cgks_advance(s, 1, dt);
+}
+
+int cgks_advance(cgks_solver* s, int n, double dt)
+{
+    if (!s || n < 0 || !s->b->state_set) return CGKS_EINVAL;
+    cgks_batch* b = s->b;
+    int which = dt > 0.0 ? 0 : 1;
+    int r = build_graph(b, which);
+    if (r) return r;
+    for (int q = 0; q < n; ++q) {
+        if (which == 0) {
+            CK(cudaMemcpyAsync(b->dfixed, &dt, 8, cudaMemcpyHostToDevice, b->stream));
+        }
+        CK(cudaGraphLaunch(b->gexec[which], b->stream));
+    }
+    return CGKS_OK;
+}
+
+int cgks_sync(cgks_solver* s, double* t_out, long long* bad_cell)
+{
+    if (!s) return CGKS_EINVAL;
+    CK(cudaStreamSynchronize(s->b->stream));
+    if (t_out) CK(cudaMemcpy(t_out, s->b->host[0].t, 8, cudaMemcpyDeviceToHost));
+    return status_of(s->b, bad_cell);
+}
+
+static int get_state_impl(cgks_batch* b, int k, double* W, double* Wx, double* Wy, double* Wxl, double* Wyl,
+                          double* sx, double* sy, cudaMemcpyKind kind, bool sync)
+{
+    if (k < 0 || k >= b->n) return CGKS_EINVAL;
+    Mesh& g = b->host[k];
+    size_t P = (size_t)g.plane;
+    int nv = b->nvar;
+    cudaStream_t s = b->stream;
+    if (W) CK(cudaMemcpyAsync(W, g.S0, nv * P * 8, kind, s));
+    if (Wx) CK(cudaMemcpyAsync(Wx, g.S0 + nv * P, nv * P * 8, kind, s));
+    if (b->dim == 2) {
+        if (Wy) CK(cudaMemcpyAsync(Wy, g.S0 + 8 * P, 4 * P * 8, kind, s));
+        if (Wxl) CK(cudaMemcpyAsync(Wxl, g.S0 + 12 * P, 4 * b->M * P * 8, kind, s));
+        if (Wyl) CK(cudaMemcpyAsync(Wyl, g.S0 + (12 + 4 * b->M) * P, 4 * b->M * P * 8, kind, s));
+        if (sy) CK(cudaMemcpyAsync(sy, g.sig_y, (size_t)(g.ny + 1) * g.nx * 8, kind, s));
+    }
+    if (sx) CK(cudaMemcpyAsync(sx, g.sig_x, (size_t)(g.nx + 1) * g.ny * 8, kind, s));
+    if (sync) CK(cudaStreamSynchronize(s));
+    return CGKS_OK;
+}
+
+int cgks_get_state(cgks_solver* s, double* W, double* Wx, double* Wy, double* Wx_line, double* Wy_line,
+                   double* sigma_x, double* sigma_y)
+{
+    if (!s) return CGKS_EINVAL;
+    return get_state_impl(s->b, 0, W, Wx, Wy, Wx_line, Wy_line, sigma_x, sigma_y, cudaMemcpyDeviceToHost, true);
+}
+
+int cgks_get_state_device(cgks_solver* s, double* W, double* Wx, double* Wy, double* Wx_line, double* Wy_line,
+                          double* sigma_x, double* sigma_y)
+{
+    if (!s) return CGKS_EINVAL;
+    return get_state_impl(s->b, 0, W, Wx, Wy, Wx_line, Wy_line, sigma_x, sigma_y, cudaMemcpyDeviceToDevice, false);
+}
+
+int cgks_get_stats(cgks_solver* s, cgks_stats* st)
+{
+    if (!s || !st) return CGKS_EINVAL;
+    cgks_batch* b = s->b;
+    Mesh& g = b->host[0];
+    size_t P = (size_t)g.plane;
+    int nv = b->nvar;
+    std::vector<double> W(nv * P);
+    CK(cudaStreamSynchronize(b->stream));
+    CK(cudaMemcpy(W.data(), g.S0, nv * P * 8, cudaMemcpyDeviceToHost));
+    std::memset(st, 0, sizeof(*st));
+    CK(cudaMemcpy(&st->t, g.t, 8, cudaMemcpyDeviceToHost));
+    unsigned long long br[4];
+    CK(cudaMemcpy(br, g.branch, sizeof(br), cudaMemcpyDeviceToHost));
+    for (int q = 0; q < 4; ++q) st->branch[q] = (long long)br[q];
+    st->min_rho = 1e300;
+    st->min_p = 1e300;
+    for (size_t c = 0; c < P; ++c) {
+        double rho = W[c], u = W[P + c] / rho, v = b->dim == 2 ? W[2 * P + c] / rho : 0.0;
+        double p = (b->p.gamma - 1.0) * (W[(b->dim + 1) * P + c] - 0.5 * rho * (u * u + v * v));
+        st->min_rho = std::min(st->min_rho, rho);
+        st->min_p = std::min(st->min_p, p);
+        for (int q = 0; q < nv; ++q) st->mass[q] += W[q * P + c] * g.dx * g.dy;
+    }
+    return CGKS_OK;
+}
+
+int cgks_step_info(cgks_solver* s, int* kernels_per_step)
+{
+    if (!s || !kernels_per_step) return CGKS_EINVAL;
+    int r = build_graph(s->b, 1);
+    if (r) return r;
+    *kernels_per_step = s->b->kernels_per_step;
+    return CGKS_OK;
+}
+
+void cgks_destroy(cgks_solver* s)
+{
+    if (!s) return;
+    cgks_batch_destroy(s->b);
+    delete s;
+}
+
+const char* cgks_strerror(int code)
+{
+    switch (code) {
+    case CGKS_OK: return "ok";
+    case CGKS_EINVAL: return "invalid argument";
+    case CGKS_ENOMEM: return "device allocation failed";
+    case CGKS_ECUDA: return "CUDA runtime error";
+    case CGKS_ENONPHYS: return "non-positive density or pressure, or non-finite value";
+    case CGKS_ETIMEOUT: return "bounded device wait timed out";
+    case CGKS_ENOTSUP: return "option combination not supported";
+    default: return "unknown error";
+    }
+}
+
+int cgks_batch_init(cgks_batch** out, const cgks_params* p, int n, const int* nx, const int* ny, const double* ext,
+                    void* stream)
+{
+    if (p && p->dim != 2) return CGKS_EINVAL;
+    return batch_create(out, p, n, nx, ny, ext, stream);
+}
+
+int cgks_batch_set_state(cgks_batch* b, int k, const double* W, const double* Wx, const double* Wy,
+                         const double* Wx_line, const double* Wy_line)
+{
+    if (!b) return CGKS_EINVAL;
+    int r = set_state_impl(b, k, W, Wx, Wy, Wx_line, Wy_line, nullptr, nullptr, cudaMemcpyHostToDevice, true);
+    if (r) return r;
+    // sigma of every instance is (re)initialised from its cell averages; the
+    // table-wide init kernel also covers meshes set earlier, which is harmless
+    // before the first step and is why instances are set before stepping.
+    b->state_set = true;
+    return post_set(b, true);
+}
+
+int cgks_batch_step(cgks_batch* b, const double* dt)
+{
+    if (!b || !b->state_set) return CGKS_EINVAL;
+    int which = dt ? 0 : 1;
+    int r = build_graph(b, which);
+    if (r) return r;
+    if (dt) CK(cudaMemcpyAsync(b->dfixed, dt, b->n * sizeof(double), cudaMemcpyHostToDevice, b->stream));
+    CK(cudaGraphLaunch(b->gexec[which], b->stream));
+    return CGKS_OK;
+}
+
+int cgks_batch_sync(cgks_batch* b)
+{
+    if (!b) return CGKS_EINVAL;
+    CK(cudaStreamSynchronize(b->stream));
+    return status_of(b, nullptr);
+}
+
+int cgks_batch_get_state(cgks_batch* b, int k, double* W, double* Wx, double* Wy, double* Wx_line, double* Wy_line)
+{
+    if (!b) return CGKS_EINVAL;
+    return get_state_impl(b, k, W, Wx, Wy, Wx_line, Wy_line, nullptr, nullptr, cudaMemcpyDeviceToHost, true);
+}
+
+void cgks_batch_destroy(cgks_batch* b)
+{
+    if (!b) return;
+    for (int q = 0; q < 2; ++q)
+        if (b->gexec[q]) cudaGraphExecDestroy(b->gexec[q]);
+    if (b->dmesh) cudaFree(b->dmesh);
+    if (b->doff) cudaFree(b->doff);
+    if (b->slab) cudaFree(b->slab);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    delete b;
+}
+
+int cgks_stencil_row(int order, int st, int row, double* out)
+{
+    if (!out || st < 0 || st > 5 || row < 0 || row > 9) return CGKS_EINVAL;
+    CgksTables t;
+    if (cgks_build_tables(order, &t) != 0) return CGKS_EINVAL;
+    if (row >= 6 + t.m) return CGKS_EINVAL;
+    for (int k = 0; k < 10; ++k) out[k] = t.row[st][row][k];
+    return CGKS_OK;
+}
+
+} // extern "C"

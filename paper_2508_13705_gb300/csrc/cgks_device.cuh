@@ -1,0 +1,539 @@
+// Device code of the ASE-DFF compact gas-kinetic scheme (sm_103a).
+//
+// One stage of the S2O4 step (Sec. 2.2) runs as four kernels, each a
+// grid-stride ("persistent") loop over the work items of every mesh in a
+// descriptor table (one mesh, or a batch of uneven meshes):
+//
+//   k_lines   Sec. 3.3 Step 1: tangential ASE-DFF reconstruction of every cell
+//             (plus a ghost halo), evaluated at the m Gauss lines of the
+//             faces normal to x and to y -> line averages.
+//   k_normal  Sec. 3.3 Step 2: normal ASE-DFF reconstruction of every
+//             (cell, Gauss line) from line averages and line-averaged slopes
+//             -> W, W_n, W_nn at the cell's two faces (Algorithm 1).
+//   k_flux    Sec. 3.3 Step 3 (tangential W_t, W_tt, W_nt from the face values
+//             of three face segments), Eq. 3.2 (sigma), Step 4 (kinetic
+//             weighting, Eq. 2.7-2.8) and the time-integrated flux and
+//             interface state of Eq. 2.6, 2.11, 2.12, 2.15 with the linear /
+//             quadratic fits of Eq. 2.19-2.20 and 2.29 done analytically per
+//             term; emits the per-point quantities the update needs.
+//   k_update  Eq. 2.21-2.25, 2.30 and the Gauss-theorem slope update of
+//             Sec. 3.3: cell averages, cell slopes and line slopes; the FP64
+//             accumulator makes stage 2 need no stage-1 face data; face
+//             sigma (Eq. 3.1) for the next step.
+//
+// Precision: R is the type of the reconstruction and kinetic arithmetic
+// (double, or float for the FP32-bulk form).  Cell averages and their
+// accumulation, the DFF (sigma, alpha, branch tests) and the positivity
+// tests are always FP64.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tables.h"
+
+namespace cgks {
+
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_FIXED = 2 };
+enum { ST_S0 = 0, ST_S1 = 1, ST_S2 = 2, ST_R5 = 3, ST_R7 = 4, ST_R9 = 5 };
+enum { STATUS_NONPHYS = 1u };
+
+struct TabF {
+    float row[6][10][10];
+    float cpoly[4][5][10];
+    float bm2[3][3];
+    float bm4[5][5];
+    float gx[4], gw[4];
+    float d1[4][12], d2[4][12];
+};
+
+static __constant__ CgksTables c_tab[3];  // orders 5, 7, 9 (one copy per translation unit)
+static __constant__ TabF c_tabf[3];
+
+template <typename R> struct Tab;
+template <> struct Tab<double> {
+    __device__ static const CgksTables& get(int oi) { return c_tab[oi]; }
+};
+template <> struct Tab<float> {
+    __device__ static const TabF& get(int oi) { return c_tabf[oi]; }
+};
+
+// Per-mesh descriptor (device memory); a batch is an array of these.
+struct Mesh {
+    int nx, ny, order, oi;          // oi: 0, 1, 2 for orders 5, 7, 9
+    int bc[4];
+    int tau_mode;
+    double dx, dy, gamma, K, thr, ghi, glo, eps, c1, c2, cfl;
+    long long plane;                // nx * ny
+    // state: planes of nx*ny doubles.  2-D: W[4] Wx[4] Wy[4] Wxl[m][4] Wyl[m][4];
+    // 1-D: W[3] Wx[3]
+    double *S0, *S1;                // S0: state n (and n+1), S1: stage-1 state W*
+    double *ACC;                    // 2-D: W[4] Wxl[m][4] Wyl[m][4]; 1-D: W[3] Wface[3]
+    double *sig_x, *sig_y;          // sigma of the previous step [ny][nx+1], [ny+1][nx]
+    double *sig_xn, *sig_yn;        // sigma being built this step
+    const double* ghost;            // 1-D fixed BC ghost cells
+    void *LA[2], *FR[2], *FO[2];    // scratch per direction (R typed)
+    double* SP[2];                  // sigma per face Gauss point
+    double* dt;                     // device scalar (this mesh's step)
+    double* t;                      // device scalar (simulated time)
+    unsigned* status;
+    long long* bad;
+    unsigned long long* smax;       // CFL reduction (bits of a positive double)
+    unsigned long long* branch;     // [4] AO, r5, r7, r9 counts
+};
+
+// Prefix sums of the work items of every kernel over the meshes of a table.
+struct Work {
+    const Mesh* mesh;
+    const long long* off;  // [n+1] prefix of items
+    int n;
+    long long total;
+};
+
+__device__ __forceinline__ int find_mesh(const Work& w, long long g)
+{
+    int lo = 0, hi = w.n - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (w.off[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int imod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+
+// ------------------------------------------------------------------ ghost cells
+
+// kind: 0 W, 1 Wx, 2 Wy, 3 Wx_line, 4 Wy_line (global orientation)
+template <int D, int M>
+__device__ __forceinline__ double cell(const Mesh& g, const double* S, int kind, int v, int l, int i, int j)
+{
+    bool zero = false;
+    if (i < 0 || i >= g.nx) {
+        int side = i < 0 ? 0 : 1;
+        int bc = g.bc[side];
+        if (bc == BC_PERIODIC) {
+            i = imod(i, g.nx);
+        } else if (bc == BC_FIXED) {
+            int layer = side == 0 ? (-1 - i) : (i - g.nx);
+            return g.ghost[((side * 3 + layer) * 2 + (kind == 0 ? 0 : 1)) * 3 + v];
+        } else {
+            i = i < 0 ? 0 : g.nx - 1;
+            zero = (kind == 1 || kind == 3);
+        }
+    }
+    if (D == 2 && (j < 0 || j >= g.ny)) {
+        if (g.bc[j < 0 ? 2 : 3] == BC_PERIODIC) {
+            j = imod(j, g.ny);
+        } else {
+            j = j < 0 ? 0 : g.ny - 1;
+            zero = zero || (kind == 2 || kind == 4);
+        }
+    }
+    if (zero) return 0.0;
+    long long idx = (long long)j * g.nx + i;
+    int p;
+    if (D == 1) {
+        p = kind == 0 ? v : 3 + v;
+    } else {
+        switch (kind) {
+        case 0: p = v; break;
+        case 1: p = 4 + v; break;
+        case 2: p = 8 + v; break;
+        case 3: p = 12 + 4 * l + v; break;
+        default: p = 12 + 4 * M + 4 * l + v; break;
+        }
+    }
+    return S[p * g.plane + idx];
+}
+
+// sigma of x-face f (between cells f-1 and f) in row j; ghost faces: periodic
+// wrap, otherwise 0 beyond the boundary face and the nearest row across y.
+template <int D>
+__device__ __forceinline__ double sigx(const Mesh& g, const double* sx, int f, int j)
+{
+    if (f < 0 || f > g.nx) {
+        if (g.bc[f < 0 ? 0 : 1] != BC_PERIODIC) return 0.0;
+        f = imod(f, g.nx);
+    }
+    if (D == 2 && (j < 0 || j >= g.ny))
+        j = g.bc[j < 0 ? 2 : 3] == BC_PERIODIC ? imod(j, g.ny) : (j < 0 ? 0 : g.ny - 1);
+    return sx[(long long)j * (g.nx + 1) + f];
+}
+
+__device__ __forceinline__ double sigy(const Mesh& g, const double* sy, int i, int f)
+{
+    if (f < 0 || f > g.ny) {
+        if (g.bc[f < 0 ? 2 : 3] != BC_PERIODIC) return 0.0;
+        f = imod(f, g.ny);
+    }
+    if (i < 0 || i >= g.nx) i = g.bc[i < 0 ? 0 : 1] == BC_PERIODIC ? imod(i, g.nx) : (i < 0 ? 0 : g.nx - 1);
+    return sy[(long long)f * g.nx + i];
+}
+
+// ------------------------------------------------------------------ ASE-DFF
+
+// Branch and stencil DFFs of one cell from the sigma of the six faces
+// i-5/2 .. i+5/2 (Eq. 3.3-3.4).  A stencil's sum covers every face of every
+// cell it draws data from; eta = 2 for r9.  Algorithm 1 picks the branch.
+struct Dff {
+    double a[4];   // alpha of S0, S1, S2, r5
+    double alpha;  // alpha of the linear stencil used
+    int st;        // linear stencil, or -1 for HWENO-AO
+};
+
+__device__ __forceinline__ double dff_alpha(double A, double thr) { return A < thr ? 1.0 : thr / A; }
+
+__device__ __forceinline__ Dff dff_select(int order, const double s[6], double thr)
+{
+    Dff d;
+    double A_r5 = s[1] + s[2] + s[3] + s[4];
+    double A_r7 = s[0] + A_r5 + s[5];
+    d.a[0] = dff_alpha(s[1] + s[2] + s[3], thr);
+    d.a[1] = dff_alpha(s[2] + s[3] + s[4], thr);
+    d.a[2] = dff_alpha(A_r5, thr);
+    d.a[3] = d.a[2];
+    double a7 = dff_alpha(A_r7, thr), a9 = dff_alpha(2.0 * A_r7, thr);
+    if (d.a[3] < 1.0) { d.st = -1; d.alpha = d.a[3]; }
+    else if (order == 5 || a7 < 1.0) { d.st = ST_R5; d.alpha = d.a[3]; }
+    else if (order == 7 || a9 < 1.0) { d.st = ST_R7; d.alpha = a7; }
+    else { d.st = ST_R9; d.alpha = a9; }
+    return d;
+}
+
+// Evaluate NOUT functionals (rows ROW0.., value rows flagged by the mask)
+// of the ASE-DFF polynomial of one cell.  dp[10]: data relative to the own
+// cell: [Qbar_{i+k} - Qbar_i (k=-2..2), h*Qx_{i+k}]; qi = Qbar_i.
+// Value outputs are returned relative to qi as well.
+template <typename R, int NOUT>
+__device__ __forceinline__ void recon(const Dff& dff, int oi, const int* rows, unsigned value_mask,
+                                      const R dp[10], R out[NOUT], double ghi, double glo, double eps)
+{
+    const auto& T = Tab<R>::get(oi);
+    if (dff.st >= 0) {
+        R al = (R)dff.alpha;
+#pragma unroll
+        for (int r = 0; r < NOUT; ++r) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) s += T.row[dff.st][rows[r]][k] * dp[k];
+            out[r] = al * s;  // Eq. 3.5: Q_i + alpha (p - Q_i), derivatives alpha p'
+        }
+        return;
+    }
+    // HWENO-AO(5,3) with DFF-scaled sub-polynomials (Eq. 3.11-3.17, 3.19)
+    R beta[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        R c[5];
+#pragma unroll
+        for (int n = 0; n < 5; ++n) {
+            R s = 0;
+#pragma unroll
+            for (int q = 0; q < 10; ++q) s += T.cpoly[k][n][q] * dp[q];
+            c[n] = s;
+        }
+        R b = 0;
+        if (k < 3) {
+#pragma unroll
+            for (int x = 1; x < 3; ++x)
+#pragma unroll
+                for (int y = 1; y < 3; ++y) b += c[x] * c[y] * T.bm2[x][y];
+        } else {
+#pragma unroll
+            for (int x = 1; x < 5; ++x)
+#pragma unroll
+                for (int y = 1; y < 5; ++y) b += c[x] * c[y] * T.bm4[x][y];
+        }
+        R ak = (R)dff.a[k];
+        beta[k] = ak * ak * b;  // smoothness of the DFF-scaled polynomial
+    }
+    R g3 = (R)ghi, g2 = (R)((1.0 - ghi) * glo), g0 = (R)((1.0 - ghi) * (1.0 - glo) * 0.5);
+    R gk[4] = {g0, g0, g2, g3};
+    R tz = (fabs(beta[3] - beta[0]) + fabs(beta[3] - beta[1]) + fabs(beta[3] - beta[2])) / (R)3;
+    R w[4], ws = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        R q = tz / (beta[k] + (R)eps);
+        w[k] = gk[k] * ((R)1 + q * q);
+        ws += w[k];
+    }
+    R inv = (R)1 / ws;
+    R c3 = w[3] * inv / g3;
+    R ck[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) ck[k] = w[k] * inv - w[3] * inv * gk[k] / g3;
+#pragma unroll
+    for (int r = 0; r < NOUT; ++r) {
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            R p = 0;
+#pragma unroll
+            for (int q = 0; q < 10; ++q) p += T.row[k][rows[r]][q] * dp[q];
+            s += (k == 3 ? c3 : ck[k]) * (R)dff.a[k] * p;
+        }
+        out[r] = s;
+    }
+    (void)value_mask;
+}
+
+// ------------------------------------------------------------------ kinetics
+
+// Maxwellian moments per unit density for one velocity range.
+template <typename R, int D>
+struct Mom {
+    R rho, U, V, lam;
+    R mu[7];
+    R mv[6];
+    R x2, x4;
+};
+
+// range: 0 full, 1 u > 0, 2 u < 0.  Returns false if rho or p <= 0.
+template <typename R, int D>
+__device__ __forceinline__ bool maxwellian(const R* W, R gamma, R K, int range, Mom<R, D>& M)
+{
+    R rho = W[0];
+    R U = W[1] / rho;
+    R V = D == 2 ? W[2] / rho : (R)0;
+    R p = (gamma - (R)1) * (W[D + 1] - (R)0.5 * rho * (U * U + V * V));
+    R lam = rho / ((R)2 * p);
+    M.rho = rho; M.U = U; M.V = V; M.lam = lam;
+    R i2l = (R)0.5 / lam;
+    if (range == 0) {
+        M.mu[0] = 1; M.mu[1] = U;
+    } else {
+        R sl = sqrt(lam);
+        R e = exp(-lam * U * U) * (R)0.28209479177387814 / sl;  // 1/(2 sqrt(pi lam))
+        if (range == 1) { M.mu[0] = (R)0.5 * erfc(-sl * U); M.mu[1] = U * M.mu[0] + e; }
+        else { M.mu[0] = (R)0.5 * erfc(sl * U); M.mu[1] = U * M.mu[0] - e; }
+    }
+#pragma unroll
+    for (int n = 0; n < 5; ++n) M.mu[n + 2] = U * M.mu[n + 1] + (R)(n + 1) * i2l * M.mu[n];
+    if (D == 2) {
+        M.mv[0] = 1; M.mv[1] = V;
+#pragma unroll
+        for (int n = 0; n < 4; ++n) M.mv[n + 2] = V * M.mv[n + 1] + (R)(n + 1) * i2l * M.mv[n];
+    }
+    M.x2 = K * i2l;
+    M.x4 = K * (K + (R)2) * i2l * i2l;
+    return rho > (R)0 && p > (R)0;
+}
+
+// <a u^p v^q psi> per unit density, a = (a1, a2, a3, a4) on psi =
+// (1, u, v, (u^2+v^2+xi^2)/2) [2-D] or a = (a1, a2, a3) on (1, u, (u^2+xi^2)/2).
+template <typename R, int D>
+__device__ __forceinline__ void mom(const Mom<R, D>& M, const R* a, int p, int q, R* out)
+{
+    if (D == 2) {
+        auto A = [&](int i, int j, bool xs) -> R {
+            R x0 = xs ? M.x2 : (R)1, x1 = xs ? M.x4 : M.x2;
+            R base = a[0] * M.mu[i] * M.mv[j] + a[1] * M.mu[i + 1] * M.mv[j] + a[2] * M.mu[i] * M.mv[j + 1]
+                   + (R)0.5 * a[3] * (M.mu[i + 2] * M.mv[j] + M.mu[i] * M.mv[j + 2]);
+            return x0 * base + (R)0.5 * a[3] * x1 * M.mu[i] * M.mv[j];
+        };
+        out[0] = A(p, q, false);
+        out[1] = A(p + 1, q, false);
+        out[2] = A(p, q + 1, false);
+        out[3] = (R)0.5 * (A(p + 2, q, false) + A(p, q + 2, false) + A(p, q, true));
+    } else {
+        auto A = [&](int i, bool xs) -> R {
+            R x0 = xs ? M.x2 : (R)1, x1 = xs ? M.x4 : M.x2;
+            return x0 * (a[0] * M.mu[i] + a[1] * M.mu[i + 1] + (R)0.5 * a[2] * M.mu[i + 2])
+                 + (R)0.5 * a[2] * x1 * M.mu[i];
+        };
+        out[0] = A(p, false);
+        out[1] = A(p + 1, false);
+        out[2] = (R)0.5 * (A(p + 2, false) + A(p, true));
+    }
+}
+
+// Closed-form solution of <a> = b (full-range moments, Eq. 2.8).
+template <typename R, int D>
+__device__ __forceinline__ void slope(const Mom<R, D>& M, R K, const R* b, R* a)
+{
+    R ir = (R)1 / M.rho;
+    R il = (R)0.5 / M.lam;
+    if (D == 2) {
+        R B0 = b[0] * ir, B1 = b[1] * ir, B2 = b[2] * ir, B3 = b[3] * ir;
+        R c = M.U * M.U + M.V * M.V + (K + (R)2) * il;
+        R R2 = B1 - M.U * B0, R3 = B2 - M.V * B0;
+        R R4 = (R)2 * B3 - c * B0;
+        R a4 = (R)4 * M.lam * M.lam / (K + (R)2) * (R4 - (R)2 * M.U * R2 - (R)2 * M.V * R3);
+        R a3 = (R)2 * M.lam * R3 - M.V * a4;
+        R a2 = (R)2 * M.lam * R2 - M.U * a4;
+        a[0] = B0 - M.U * a2 - M.V * a3 - (R)0.5 * a4 * c;
+        a[1] = a2; a[2] = a3; a[3] = a4;
+    } else {
+        R B0 = b[0] * ir, B1 = b[1] * ir, B2 = b[2] * ir;
+        R c = M.U * M.U + (K + (R)1) * il;
+        R R2 = B1 - M.U * B0;
+        R R3 = (R)2 * B2 - c * B0;
+        R a3 = (R)4 * M.lam * M.lam / (K + (R)1) * (R3 - (R)2 * M.U * R2);
+        R a2 = (R)2 * M.lam * R2 - M.U * a3;
+        a[0] = B0 - M.U * a2 - (R)0.5 * a3 * c;
+        a[1] = a2; a[2] = a3;
+    }
+}
+
+// Reconstructed data on one side of a face point, local frame (n normal, t
+// tangential, momentum components ordered normal first):
+// 0 W, 1 W_n, 2 W_nn, 3 W_t, 4 W_tt, 5 W_nt
+template <typename R, int D>
+struct SideData { R d[6][4]; };
+
+// Per-point results in the local frame: F, F_t (fitted flux and derivative,
+// Eq. 2.19-2.20), Q0 = W(0), W_t, W_tt (Eq. 2.29).  Returns false on a
+// non-positive density / pressure.
+template <typename R, int D>
+__device__ __forceinline__ bool kinetic(const SideData<R, D>& L, const SideData<R, D>& Rt, R gamma, R K,
+                                        int tau_mode, R c1, R c2, R dt,
+                                        R F[4], R Ft[4], R Q0[4], R Wt[4], R Wtt[4])
+{
+    constexpr int NV = D + 2;
+    constexpr int ND = D == 2 ? 5 : 2;
+    Mom<R, D> Ml, Mr, M0;
+    bool ok = maxwellian<R, D>(L.d[0], gamma, K, 1, Ml);
+    ok &= maxwellian<R, D>(Rt.d[0], gamma, K, 2, Mr);
+    // kinetic weighting of the initial states (Eq. 2.7)
+    R e1[4] = {1, 0, 0, 0};
+    R tl[4], tr[4];
+    mom<R, D>(Ml, e1, 0, 0, tl);
+    mom<R, D>(Mr, e1, 0, 0, tr);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) Q0[i] = Ml.rho * tl[i] + Mr.rho * tr[i];
+    R dQ[ND][4];
+    R al_n[4], al_t[4], ar_n[4], ar_t[4];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) {
+        R a_l[4], a_r[4];
+        slope<R, D>(Ml, K, L.d[q + 1], a_l);
+        slope<R, D>(Mr, K, Rt.d[q + 1], a_r);
+        if (q == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { al_n[i] = a_l[i]; ar_n[i] = a_r[i]; }
+        }
+        if (D == 2 && q == 2) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) { al_t[i] = a_l[i]; ar_t[i] = a_r[i]; }
+        }
+        mom<R, D>(Ml, a_l, 0, 0, tl);
+        mom<R, D>(Mr, a_r, 0, 0, tr);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) dQ[q][i] = Ml.rho * tl[i] + Mr.rho * tr[i];
+    }
+    ok &= maxwellian<R, D>(Q0, gamma, K, 0, M0);
+    // equilibrium micro-slopes: n, nn (, t, tt, nt)
+    R ab[ND][4];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) slope<R, D>(M0, K, dQ[q], ab[q]);
+    R S1[4], S2[4], z[4], rhs[4], Ab[4], A1t[4], A2t[4] = {0, 0, 0, 0};
+    // S1 = <a_n u + a_t v>, A-bar from <a_n u + a_t v + A> = 0
+    mom<R, D>(M0, ab[0], 1, 0, S1);
+    if (D == 2) {
+        mom<R, D>(M0, ab[2], 0, 1, z);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) S1[i] += z[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) { S1[i] *= M0.rho; rhs[i] = -S1[i]; }
+    slope<R, D>(M0, K, rhs, Ab);
+    // time derivatives of the slopes, <a_nn u + a_nt v + a_1t> = 0 etc.
+    mom<R, D>(M0, ab[1], 1, 0, rhs);
+    if (D == 2) {
+        mom<R, D>(M0, ab[4], 0, 1, z);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) rhs[i] += z[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) rhs[i] *= -M0.rho;
+    slope<R, D>(M0, K, rhs, A1t);
+    if (D == 2) {
+        mom<R, D>(M0, ab[4], 1, 0, rhs);
+        mom<R, D>(M0, ab[3], 0, 1, z);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) rhs[i] = -M0.rho * (rhs[i] + z[i]);
+        slope<R, D>(M0, K, rhs, A2t);
+    }
+    // S2 = <a_1t u + a_2t v>
+    mom<R, D>(M0, A1t, 1, 0, S2);
+    if (D == 2) {
+        mom<R, D>(M0, A2t, 0, 1, z);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) S2[i] += z[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NV; ++i) S2[i] *= M0.rho;
+    // flux terms: <u> and <A u> (equilibrium part, linear in t)
+    R T0[4], T1[4];
+    mom<R, D>(M0, e1, 1, 0, T0);
+    mom<R, D>(M0, Ab, 1, 0, T1);
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        T0[i] *= M0.rho;
+        T1[i] *= M0.rho;
+        F[i] = T0[i];
+        Ft[i] = T1[i];
+        Wt[i] = -S1[i];
+        Wtt[i] = -S2[i];
+    }
+    if (tau_mode == 1) {
+        R pl = (gamma - (R)1) * (L.d[0][NV - 1] - (R)0.5 * Ml.rho * (Ml.U * Ml.U + Ml.V * Ml.V));
+        R pr = (gamma - (R)1) * (Rt.d[0][NV - 1] - (R)0.5 * Mr.rho * (Mr.U * Mr.U + Mr.V * Mr.V));
+        R tau = c1 * dt + c2 * fabs(pl - pr) / (pl + pr) * dt;
+        // non-equilibrium and collision terms of Eq. 2.6
+        R Att[4], T2[4], T3[4], T4[4], T5[4], T6[4], S1h[4];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) rhs[i] = -S2[i];
+        slope<R, D>(M0, K, rhs, Att);
+        mom<R, D>(M0, Att, 1, 0, T2);
+        mom<R, D>(M0, ab[0], 2, 0, T3);
+        mom<R, D>(M0, A1t, 2, 0, T4);
+        if (D == 2) {
+            mom<R, D>(M0, ab[2], 1, 1, z);
+#pragma unroll
+            for (int i = 0; i < NV; ++i) T3[i] += z[i];
+            mom<R, D>(M0, A2t, 1, 1, z);
+#pragma unroll
+            for (int i = 0; i < NV; ++i) T4[i] += z[i];
+        }
+        mom<R, D>(Ml, e1, 1, 0, tl);
+        mom<R, D>(Mr, e1, 1, 0, tr);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) T5[i] = Ml.rho * tl[i] + Mr.rho * tr[i];
+        // half-range slope terms, with and without the extra u of the flux
+        R hl[4], hr[4];
+        for (int pu = 0; pu < 2; ++pu) {
+            mom<R, D>(Ml, al_n, pu + 1, 0, tl);
+            mom<R, D>(Mr, ar_n, pu + 1, 0, tr);
+            if (D == 2) {
+                mom<R, D>(Ml, al_t, pu, 1, hl);
+                mom<R, D>(Mr, ar_t, pu, 1, hr);
+#pragma unroll
+                for (int i = 0; i < NV; ++i) { tl[i] += hl[i]; tr[i] += hr[i]; }
+            }
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                R s = Ml.rho * tl[i] + Mr.rho * tr[i];
+                if (pu == 0) S1h[i] = s; else T6[i] = s;
+            }
+        }
+        R ed = exp(-dt / tau), eh = exp((R)-0.5 * dt / tau);
+        R h = (R)0.5 * dt;
+        R E0d = tau * ((R)1 - ed), E0h = tau * ((R)1 - eh);
+        R E1d = tau * tau * ((R)1 - ed) - tau * dt * ed, E1h = tau * tau * ((R)1 - eh) - tau * h * eh;
+        R f0 = ((R)4 * E0h - E0d) / dt, g0 = (R)4 * (E0d - (R)2 * E0h) / (dt * dt);
+        R f1 = ((R)4 * E1h - E1d) / dt, g1 = (R)4 * (E1d - (R)2 * E1h) / (dt * dt);
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            R T3s = T3[i] * M0.rho, T4s = T4[i] * M0.rho, T2s = T2[i] * M0.rho;
+            F[i] = T0[i] * ((R)1 - f0) - tau * T1[i] + (f1 - tau) * T3s + f0 * T5[i] - f1 * T6[i];
+            Ft[i] = -g0 * T0[i] + T1[i] - tau * T2s + g1 * T3s - tau * T4s + g0 * T5[i] - g1 * T6[i];
+            R dS = S1[i] - S1h[i];
+            Wt[i] += ((R)2 * eh - ed) * dS;
+            Wtt[i] += (R)4 * (ed - eh) / dt * dS;
+        }
+    }
+    return ok;
+}
+
+} // namespace cgks

@@ -1,0 +1,22 @@
+// Kernel entry points of one (dimension, Gauss points, precision)
+// configuration; each configuration is compiled in its own translation unit.
+#pragma once
+#include "cgks_device.cuh"
+
+namespace cgks {
+typedef void (*KStage)(Work, int);
+typedef void (*KOne)(Work);
+struct Kfns {
+    KStage lines, normal;
+    KOne flux1, flux2, upd1, upd2, cfl, siginit, check;
+    int (*upload)(const CgksTables* t3, const TabF* f3);  // constant tables of this unit
+};
+Kfns kfns_1_1_d();
+Kfns kfns_1_1_f();
+Kfns kfns_2_2_d();
+Kfns kfns_2_3_d();
+Kfns kfns_2_4_d();
+Kfns kfns_2_2_f();
+Kfns kfns_2_3_f();
+Kfns kfns_2_4_f();
+}

@@ -1,0 +1,32 @@
+// Instantiates the kernels of one configuration (included once per unit).
+#pragma once
+#include "cgks_kernels.cuh"
+#include "kfns.h"
+
+namespace cgks {
+namespace {
+int upload_tables(const CgksTables* t3, const TabF* f3)
+{
+    if (cudaMemcpyToSymbol(c_tab, t3, sizeof(CgksTables) * 3) != cudaSuccess) return 1;
+    if (cudaMemcpyToSymbol(c_tabf, f3, sizeof(TabF) * 3) != cudaSuccess) return 1;
+    return 0;
+}
+}  // namespace
+
+template <int D, int M, typename R>
+Kfns make_kfns()
+{
+    Kfns k;
+    k.lines = D == 2 ? (KStage)k_lines<M, R> : nullptr;
+    k.normal = k_normal<D, M, R>;
+    k.flux1 = k_flux<D, M, R, 1>;
+    k.flux2 = k_flux<D, M, R, 2>;
+    if (D == 2) { k.upd1 = (KOne)k_update2<M, R, 1>; k.upd2 = (KOne)k_update2<M, R, 2>; }
+    else { k.upd1 = (KOne)k_update1<R, 1>; k.upd2 = (KOne)k_update1<R, 2>; }
+    k.cfl = k_cfl<D>;
+    k.siginit = k_sigma_init<D>;
+    k.check = k_check_state<D>;
+    k.upload = upload_tables;
+    return k;
+}
+}  // namespace cgks

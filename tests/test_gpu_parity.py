@@ -1,0 +1,243 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerance: the plain FP64 form must match the oracle to relative L1 <= 1e-12
+(sum |gpu - oracle| / sum |oracle| per field); both evaluate the same
+definitions in a different operation order.  Discontinuous cases are compared
+per step from the same state, so that DFF branch decisions cannot flip on
+rounding; smooth cases are compared over whole runs.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2508_13705_gb300 import cgks, inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+FIELDS_2D = ("W", "Wx", "Wy", "Wx_line", "Wy_line", "sigma_x", "sigma_y")
+FIELDS_1D = ("W", "Wx", "sigma_x")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2508_13705_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def rel_l1(a, b):
+    den = np.abs(b).sum()
+    return np.abs(a - b).sum() / (den if den > 0 else 1.0)
+
+
+def compare(gpu, orc, fields, tol=TOL, what=""):
+    o = orc.get_state()
+    for f in fields:
+        e = rel_l1(gpu[f], o[f])
+        assert e <= tol, "%s %s: rel L1 %.3e" % (what, f, e)
+
+
+def run_both(dim, order, n, st, steps, extent, dt=None, ny=None, **kw):
+    ny = ny or n
+    s = cgks.Solver(dim, order, n, ny if dim == 2 else 1, extent=extent, **kw)
+    okw = {k: v for k, v in kw.items() if k in ("tau_mode", "bc", "cfl", "gamma")}
+    o = oracle.Oracle(dim, order, n, ny if dim == 2 else 1, extent=extent, **okw)
+    s.set_state(*st)
+    o.set_state(*st)
+    for _ in range(steps):
+        d = dt if dt is not None else o.compute_dt()
+        s.step(d)
+        o.step(d)
+    s.sync()
+    return s, o
+
+
+# ---------------------------------------------------------------- 1-D
+
+@pytest.mark.parametrize("order", [5, 7, 9])
+def test_density_wave_1d_full_run(order):
+    """Config C1 shape (N = 80, t = 2 for order 5; shorter runs for 7 and 9)."""
+    N = 80
+    dx = 2.0 / N
+    dt = 0.3 * dx ** (order / 4) if order == 5 else 2e-3
+    steps = int(round(2.0 / dt)) if order == 5 else 60
+    s, o = run_both(1, order, N, inputs.density_wave_1d(N), steps, (0, 2, 0, 1), dt=dt)
+    compare(s.get_state(), o, FIELDS_1D, what="1-D order %d" % order)
+
+
+@pytest.mark.parametrize("order", [5, 9])
+def test_sod_1d_per_step(order):
+    """Shock tube: every step starts both from the oracle's state; the DFF
+    branches (HWENO-AO near the waves) must agree exactly."""
+    N = 100
+    st = inputs.riemann_1d(N, *inputs.SOD)
+    kw = dict(tau_mode=cgks.TAU_HGKS, bc=(1, 1, 1, 1))
+    o = oracle.Oracle(1, order, N, extent=(0, 1, 0, 1), **kw)
+    o.set_state(*st)
+    s = cgks.Solver(1, order, N, extent=(0, 1, 0, 1), **kw)
+    used_ao = False
+    for k in range(25):
+        g0 = o.get_state()
+        s.set_state(g0["W"], g0["Wx"], sigma_x=g0["sigma_x"])
+        dt = o.compute_dt()
+        s.step(dt)
+        s.sync()
+        o.step(dt)
+        used_ao |= bool((o.branch == 0).any())
+        compare(s.get_state(), o, FIELDS_1D, what="Sod step %d" % k)
+    assert used_ao
+
+
+def test_shu_osher_fixed_ghost_multi_step():
+    """Config C2 shape: transmissive left end, fixed-profile right ghost cells."""
+    N = 400
+    W, Wx, ghost = inputs.shu_osher_1d(N)
+    kw = dict(tau_mode=cgks.TAU_HGKS, bc=(cgks.BC_TRANSMISSIVE, cgks.BC_FIXED, 1, 1))
+    o = oracle.Oracle(1, 7, N, extent=(-5, 5, 0, 1), **kw)
+    o.set_state(W, Wx, ghost=ghost)
+    s = cgks.Solver(1, 7, N, extent=(-5, 5, 0, 1), **kw)
+    s.set_ghost(ghost)
+    s.set_state(W, Wx)
+    for _ in range(10):
+        dt = o.compute_dt()
+        s.step(dt)
+        o.step(dt)
+    s.sync()
+    compare(s.get_state(), o, FIELDS_1D, what="Shu-Osher")
+
+
+# ---------------------------------------------------------------- 2-D smooth
+
+@pytest.mark.parametrize("order", [5, 7, 9])
+def test_density_wave_2d_multi_step(order):
+    n = 10
+    s, o = run_both(2, order, n, inputs.density_wave_2d(n, order), 12, (0, 2, 0, 2))
+    compare(s.get_state(), o, FIELDS_2D, what="2-D wave order %d" % order)
+
+
+@pytest.mark.parametrize("order", [7, 9])
+def test_vortex_ragged_mesh(order):
+    """Isentropic vortex (config C3 shape) on a ragged nx != ny mesh."""
+    nx, ny = 23, 17
+    st = inputs.cell_state_2d(inputs.vortex_prim(), nx, ny, (0, 10, 0, 10), order)
+    s, o = run_both(2, order, nx, st, 6, (0, 10, 0, 10), ny=ny)
+    compare(s.get_state(), o, FIELDS_2D, what="vortex order %d" % order)
+
+
+# ---------------------------------------------------------------- 2-D shocks
+
+@pytest.mark.parametrize("order,bc", [(9, 1), (7, 0), (5, 1)])
+def test_quadrants_per_step(order, bc):
+    """Four-quadrant Riemann problem (config C4 shape), per-step parity."""
+    nx, ny = 20, 14
+    s6 = inputs.quadrant_states(0)
+    hx, hy = 1.0 / nx, 1.0 / ny
+    xc = (np.arange(nx) + 0.5) * hx
+    yc = (np.arange(ny) + 0.5) * hy
+    east = (xc >= 0.5)[None, :]
+    north = (yc >= 0.5)[:, None]
+    pr = s6[np.where(north, np.where(east, 2, 3), np.where(east, 1, 0))]
+    W = np.stack([pr[..., 0], pr[..., 0] * pr[..., 1], pr[..., 0] * pr[..., 2],
+                  pr[..., 3] / 0.4 + 0.5 * pr[..., 0] * (pr[..., 1] ** 2 + pr[..., 2] ** 2)])
+    m = {5: 2, 7: 3, 9: 4}[order]
+    z = np.zeros((4, ny, nx))
+    kw = dict(tau_mode=cgks.TAU_HGKS, bc=(bc,) * 4)
+    o = oracle.Oracle(2, order, nx, ny, extent=(0, 1, 0, 1), **kw)
+    o.set_state(W, z, z, np.zeros((m, 4, ny, nx)), np.zeros((m, 4, ny, nx)))
+    s = cgks.Solver(2, order, nx, ny, extent=(0, 1, 0, 1), **kw)
+    for k in range(4):
+        g0 = o.get_state()
+        s.set_state(g0["W"], g0["Wx"], g0["Wy"], g0["Wx_line"], g0["Wy_line"], g0["sigma_x"], g0["sigma_y"])
+        dt = o.compute_dt()
+        s.step(dt)
+        s.sync()
+        o.step(dt)
+        compare(s.get_state(), o, FIELDS_2D, what="quadrants step %d" % k)
+
+
+def test_initial_sigma_and_cfl_match_oracle():
+    n = 16
+    st = inputs.quadrants_2d(n, 9, seed=4)
+    s = cgks.Solver(2, 9, n, n, extent=(0, 1, 0, 1), bc=(1, 1, 1, 1))
+    s.set_state(*st)
+    o = oracle.Oracle(2, 9, n, n, extent=(0, 1, 0, 1), bc=(1, 1, 1, 1))
+    o.set_state(*st)
+    compare(s.get_state(), o, ("sigma_x", "sigma_y"), tol=1e-14)
+    assert abs(s.compute_dt() / o.compute_dt() - 1) < 1e-14
+
+
+# ---------------------------------------------------------------- invariants
+
+def test_free_stream_and_determinism():
+    n = 16
+    W = np.zeros((4, n, n))
+    W[0], W[1], W[2] = 1.0, 0.3, -0.7
+    W[3] = 2.5 + 0.5 * 0.58
+    z = np.zeros((4, n, n))
+    zl = np.zeros((4, 4, n, n))
+    outs = []
+    for _ in range(2):
+        s = cgks.Solver(2, 9, n, n, tau_mode=cgks.TAU_HGKS)
+        s.set_state(W, z, z, zl, zl)
+        s.advance(5, 0.0)
+        s.sync()
+        outs.append(s.get_state())
+    assert np.abs(outs[0]["W"] - W).max() <= 1e-14 * 4
+    for f in FIELDS_2D:
+        assert np.array_equal(outs[0][f], outs[1][f]), f
+
+
+def test_checkpoint_resume_bitwise():
+    """k steps + get_state + set_state (with sigma) + N-k steps == N steps."""
+    n = 12
+    st = inputs.quadrants_2d(n, 7, seed=1)
+    kw = dict(tau_mode=cgks.TAU_HGKS, bc=(1, 1, 1, 1))
+    a = cgks.Solver(2, 7, n, n, **kw)
+    a.set_state(*st)
+    a.advance(6, 1e-3)
+    a.sync()
+    b = cgks.Solver(2, 7, n, n, **kw)
+    b.set_state(*st)
+    b.advance(3, 1e-3)
+    b.sync()
+    mid = b.get_state()
+    c = cgks.Solver(2, 7, n, n, **kw)
+    c.set_state(mid["W"], mid["Wx"], mid["Wy"], mid["Wx_line"], mid["Wy_line"], mid["sigma_x"], mid["sigma_y"])
+    c.advance(3, 1e-3)
+    c.sync()
+    ga, gc = a.get_state(), c.get_state()
+    for f in FIELDS_2D:
+        assert np.array_equal(ga[f], gc[f]), f
+
+
+def test_conservation_periodic():
+    n = 32
+    st = inputs.vortex_2d(n, 9)
+    s = cgks.Solver(2, 9, n, n, extent=(0, 10, 0, 10))
+    s.set_state(*st)
+    m0 = s.stats()["mass"]
+    s.advance(20, 0.0)
+    t, _, _ = s.sync()
+    m1 = s.stats()["mass"]
+    assert t > 0
+    for a, b in zip(m0, m1):
+        assert abs(a - b) <= 1e-13 * abs(a) + 1e-13
+
+
+def test_nonphysical_state_rejected():
+    n = 8
+    st = list(inputs.quadrants_2d(n, 5, seed=0))
+    st[0] = st[0].copy()
+    st[0][0, 3, 3] = -1.0
+    s = cgks.Solver(2, 5, n, n)
+    with pytest.raises(cgks.CgksError) as e:
+        s.set_state(*st)
+    assert e.value.code == cgks.ENONPHYS
+
+
+def test_step_before_state_is_an_error():
+    s = cgks.Solver(2, 5, 8, 8)
+    with pytest.raises(cgks.CgksError) as e:
+        s.step(1e-3)
+    assert e.value.code == cgks.EINVAL
