@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Throughput of the ASE-DFF compact gas-kinetic S2O4 step on GB300.
+
+Workload (one "step" = one full two-stage S2O4 step, CFL time step computed
+on the device, of the whole mesh): 2-D Euler, gamma 1.4, periodic [0,10]^2,
+2048^2 cells, isentropic vortex of strength 5 (background rho = u = v = p = 1),
+ninth order ASE-DFF(9,7,5,3), CFL 0.5, tau = 0.  Synthetic, seeded-free
+(deterministic) input generated by ``paper_2508_13705_gb300.inputs``.
+
+Metric: Mcell-stage/s = cells x 2 stages x steps / device time.  The headline
+``value`` is the FP32-bulk form; the plain FP64 form is measured on the same
+mesh and reported under ``fp64_plain``; ``accuracy`` compares the two forms'
+L1 density error at t = 10 (one period, exact solution = initial data) on a
+256^2 mesh.  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_PEAK_LANES = 128       # FP32 lanes per SM (Blackwell)
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate (non-tensor), profiling recipe
+HBM_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+# Algorithmic FP operations per face Gauss point of the flux kernel (stage 1,
+# tau = 0, 2-D, order 9): FADD + FMUL + 2 FFMA (+ DADD/DMUL/2 DFMA) counted by
+# ncu on the flux kernel of a small mesh, divided by the face points of the
+# launch (the kernel evaluates every face point exactly once).
+FLOPS_PER_POINT = {("fp32", 9): None, ("fp64", 9): None}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=2048)
+    ap.add_argument("--order", type=int, default=9)
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(n):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if n > 0 else "gloo")
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def max_over_ranks(pg, x):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.2)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def vortex_inputs(n, order, nq=4):
+    from paper_2508_13705_gb300 import inputs
+    return inputs.cell_state_2d(inputs.vortex_prim(), n, n, (0.0, 10.0, 0.0, 10.0), order, nq=nq)
+
+
+def face_points(n, order):
+    m = (order - 1) // 2
+    return 2 * (n + 1) * n * m
+
+
+def peaks():
+    try:
+        return json.load(open(HBM_PEAKS))
+    except (OSError, ValueError):
+        return {}
+
+
+def gpu_peak_tflops(precision, sm_count, mhz):
+    if precision == "fp32":
+        return sm_count * FP32_PEAK_LANES * 2 * mhz * 1e6 / 1e12
+    return FP64_NOMINAL_TFLOPS * mhz / 2070.0
+
+
+def run_gpu_form(torch, cgks, st, n, order, precision, steps, warmup, stream):
+    s = cgks.Solver(2, order, n, n, extent=(0.0, 10.0, 0.0, 10.0), precision=precision,
+                    stream=stream.cuda_stream)
+    s.set_state(*st)
+    s.advance(warmup, 0.0)
+    s.sync()
+    return s
+
+
+def cpu_oracle_rate(order, n_sample, steps):
+    """FP64 CPU oracle on a bounded sample of the workload (same problem, smaller mesh)."""
+    import oracle
+    oracle.build()
+    st = vortex_inputs(n_sample, order, nq=4)
+    o = oracle.Oracle(2, order, n_sample, n_sample, extent=(0.0, 10.0, 0.0, 10.0))
+    o.set_state(*st)
+    o.step()  # first call loads the library
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step()
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n_sample * n_sample * 2 * steps / el / 1e6, cores, el
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return reference_arm(a)
+    import torch
+
+    from paper_2508_13705_gb300 import build, cgks
+    rank, world, local, pg = dist_setup(a.gpus)
+    torch.cuda.set_device(local)
+    if rank == 0:
+        build.build()
+    barrier(pg)
+    n, order = a.n, a.order
+    t_in = time.perf_counter()
+    st = vortex_inputs(n, order)
+    t_in = time.perf_counter() - t_in
+    stream = torch.cuda.Stream()
+    cells = n * n
+
+    # ---------------- FP32-bulk form (headline)
+    s32 = run_gpu_form(torch, cgks, st, n, order, cgks.FP32_BULK, a.steps, a.warmup, stream)
+    kps = s32.kernels_per_step()
+    clk = ClockSampler(local)
+    clk.start()
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s32.advance(a.steps, 0.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    ms32 = max_over_ranks(pg, e0.elapsed_time(e1))
+    clocks = clk.stop()
+    _, rc32, _ = s32.sync(raise_on_error=False)
+    dt = s32.compute_dt()
+    prof32 = s32.profile_step(dt)
+
+    # ---------------- FP64 plain form, same mesh
+    k64 = max(2, a.steps // 5)
+    s64 = run_gpu_form(torch, cgks, st, n, order, cgks.FP64, k64, 1, stream)
+    barrier(pg)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s64.advance(k64, 0.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(pg)
+    ms64 = max_over_ranks(pg, e0.elapsed_time(e1))
+    _, rc64, _ = s64.sync(raise_on_error=False)
+    prof64 = s64.profile_step(s64.compute_dt())
+    s64.close()
+
+    # ---------------- end to end: host (pinned) state in, step, state out
+    k_e2e = max(1, min(a.steps, 5))
+    names = ("W", "Wx", "Wy", "Wx_line", "Wy_line", "sigma_x", "sigma_y")
+    g = s32.get_state()
+    pinned = {k: torch.from_numpy(g[k]).pin_memory() for k in names}
+    host = {k: pinned[k].numpy() for k in names}
+    bytes_state = sum(v.nbytes for v in host.values())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        s32.set_state(*[host[k] for k in names])
+        s32.step(0.0)
+        st_out = s32.get_state()
+        for k in names:
+            host[k][...] = st_out[k]
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
+    s32.close()
+
+    value = world * cells * 2 * a.steps / (ms32 / 1e3) / 1e6
+    v64 = world * cells * 2 * k64 / (ms64 / 1e3) / 1e6
+    e2e_v = world * cells * 2 * k_e2e / e2e_s / 1e6
+
+    # ---------------- roofline of the dominant kernel (plain ALU arithmetic)
+    props = torch.cuda.get_device_properties(local)
+    sm_count = props.multi_processor_count
+    mhz = clocks.get("sm_max_mhz") or 2070.0
+    names_k = {0: "lines", 1: "normal", 2: "flux", 3: "update", 4: "dt"}
+
+    def roof(prof, precision):
+        top = max(prof, key=lambda x: x[1])
+        kid, kms = top
+        total = sum(x[1] for x in prof)
+        fpp = FLOPS_PER_POINT.get((precision, order))
+        peak = gpu_peak_tflops(precision, sm_count, mhz)
+        ach = None if fpp is None or kid % 10 != 2 else fpp * face_points(n, order) / (kms / 1e3) / 1e12
+        return {"bound": "alu", "kernel": "k_flux stage %d" % (kid // 10) if kid % 10 == 2 else names_k[kid % 10],
+                "achieved": ach, "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": None if ach is None else ach / peak, "traffic": None,
+                "share_of_step": kms / total,
+                "peak_basis": ("%d SMs x %d FP32 lanes x 2 x %.0f MHz" % (sm_count, FP32_PEAK_LANES, mhz))
+                if precision == "fp32" else "nominal FP64 1.25 TFLOP/s at 2070 MHz, scaled to %.0f MHz" % mhz,
+                "kernels_ms": {("s%d_" % (k // 10) if k >= 10 else "") + names_k[k % 10]: round(v, 4) for k, v in prof}}
+
+    line = {
+        "metric": "Mcell-stage/s 2D 9th-order, FP32 form vs FP64 plain at fixed L1 err; %roofline",
+        "value": round(value, 3), "unit": "Mcell-stage/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": round(ms32 / a.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "isentropic vortex 2-D, periodic [0,10]^2, %dx%d cells, order %d, CFL 0.5, tau 0"
+                               % (n, n, order), "precision": "FP32 bulk, FP64 cell averages and accumulation",
+                   "global_batch": world, "mesh": [n, n], "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (state %.2f GB per replica)" % (bytes_state / 1e9)},
+        "fp64_plain": {"value": round(v64, 3), "unit": "Mcell-stage/s", "steps": k64,
+                       "ms_per_step": round(ms64 / k64, 4), "status": rc64,
+                       "roofline": roof(prof64, "fp64")},
+        "roofline": roof(prof32, "fp32"),
+        "clocks": clocks,
+        "e2e": {"value": round(e2e_v, 3), "unit": "Mcell-stage/s", "h2d_bytes_per_step": bytes_state,
+                "d2h_bytes_per_step": bytes_state, "steps": k_e2e},
+        "gpu_launches": kps * a.steps,
+        "status": rc32,
+        "input_gen_s": round(t_in, 2),
+    }
+    if rank == 0 and not a.no_accuracy:
+        line["accuracy"] = accuracy(torch, cgks, order, stream)
+    if rank == 0 and not a.no_cpu:
+        rate, cores, el = cpu_oracle_rate(order, 128, 2)
+        line["cpu_baseline"] = {"value": round(rate, 5), "unit": "Mcell-stage/s", "cores": cores, "kind": "oracle",
+                                "sample": "2 steps of the same vortex problem on a 128^2 mesh (%.1f s)" % el}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def accuracy(torch, cgks, order, stream, n=256, t_end=10.0):
+    """L1 density error of both forms at t = 10 (one period) on n^2 cells."""
+    from paper_2508_13705_gb300 import inputs
+    st = inputs.vortex_2d(n, order)
+    out = {"mesh": [n, n], "t": t_end}
+    for name, prec in (("fp64", cgks.FP64), ("fp32", cgks.FP32_BULK)):
+        s = cgks.Solver(2, order, n, n, extent=(0.0, 10.0, 0.0, 10.0), precision=prec, stream=stream.cuda_stream)
+        s.set_state(*st)
+        t = 0.0
+        steps = 0
+        while t < t_end - 1e-12:
+            dt = min(s.compute_dt(), t_end - t)
+            s.step(dt)
+            t += dt
+            steps += 1
+        _, rc, _ = s.sync(raise_on_error=False)
+        W = s.get_state()["W"]
+        out["l1_" + name] = float(np.abs(W[0] - st[0][0]).mean())
+        out["status_" + name] = rc
+        out["steps"] = steps
+        s.close()
+    out["fp32_over_fp64"] = out["l1_fp32"] / out["l1_fp64"]
+    out["within_10pct"] = out["fp32_over_fp64"] <= 1.10
+    return out
+
+
+def reference_arm(a):
+    """The FP64 CPU oracle, timed on the host cores, on bounded samples."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    n_sample = 96
+    order = a.order
+    st = vortex_inputs(n_sample, order)
+    o = oracle.Oracle(2, order, n_sample, n_sample, extent=(0.0, 10.0, 0.0, 10.0))
+    o.set_state(*st)
+    for _ in range(a.warmup):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        o.step()
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    v = n_sample * n_sample * 2 * a.steps / el / 1e6
+    sample = "the %dx%d vortex problem (same physics and order as the %d^2 workload), one S2O4 step per step" % (
+        n_sample, n_sample, a.n)
+    line = {"impl": "reference", "metric": "Mcell-stage/s 2D 9th-order, FP32 form vs FP64 plain at fixed L1 err; %roofline",
+            "value": round(v, 5), "unit": "Mcell-stage/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": round(el / a.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "isentropic vortex 2-D, periodic [0,10]^2, %dx%d cells, order %d, CFL 0.5, tau 0"
+                                   % (a.n, a.n, order), "sampled_mesh": [n_sample, n_sample]},
+            "cpu_baseline": {"value": round(v, 5), "unit": "Mcell-stage/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 5), "unit": "Mcell-stage/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

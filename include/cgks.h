@@ -154,6 +154,14 @@ int cgks_get_stats(cgks_solver* s, cgks_stats* st);
 /* Number of graph nodes (kernel launches) one CFL step makes. */
 int cgks_step_info(cgks_solver* s, int* kernels_per_step);
 
+/* Diagnostics: run one fixed-dt step (dt > 0) kernel by kernel outside the
+ * graph, with CUDA events on the solver's stream between launches.  ms[k]
+ * receives the device time of launch k and ids[k] its kernel:
+ * 0 lines, 1 normal, 2 flux, 3 update, 4 dt (stage s launches carry
+ * 10*s + id).  *n is the capacity on entry and the count on exit (<= 16).
+ * Advances the state like cgks_step. */
+int cgks_profile_step(cgks_solver* s, double dt, float* ms, int* ids, int* n);
+
 void cgks_destroy(cgks_solver* s);
 const char* cgks_strerror(int code);
 

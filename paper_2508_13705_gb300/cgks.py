@@ -27,7 +27,7 @@ EXPORTS = ("cgks_default_params", "cgks_init_mesh", "cgks_set_state", "cgks_set_
            "cgks_get_state", "cgks_get_state_device", "cgks_get_stats", "cgks_step_info",
            "cgks_destroy", "cgks_strerror", "cgks_batch_init", "cgks_batch_set_state",
            "cgks_batch_step", "cgks_batch_sync", "cgks_batch_get_state", "cgks_batch_destroy",
-           "cgks_stencil_row")
+           "cgks_stencil_row", "cgks_profile_step")
 
 
 class Params(ctypes.Structure):
@@ -87,6 +87,8 @@ def lib():
         L.cgks_batch_destroy.argtypes = [vp]
         L.cgks_batch_destroy.restype = None
         L.cgks_stencil_row.argtypes = [ip, ip, ip, dp]
+        L.cgks_profile_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ctypes.c_float),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         _lib = L
     return _lib
 
@@ -216,6 +218,14 @@ class Solver:
         n = ctypes.c_int()
         _check(lib().cgks_step_info(self.h, ctypes.byref(n)), "cgks_step_info")
         return n.value
+
+    def profile_step(self, dt):
+        """One fixed-dt step kernel by kernel: list of (kernel id, device ms)."""
+        ms = (ctypes.c_float * 16)()
+        ids = (ctypes.c_int * 16)()
+        n = ctypes.c_int(16)
+        _check(lib().cgks_profile_step(self.h, float(dt), ms, ids, ctypes.byref(n)), "cgks_profile_step")
+        return [(ids[k], ms[k]) for k in range(n.value)]
 
     def close(self):
         if getattr(self, "h", None):

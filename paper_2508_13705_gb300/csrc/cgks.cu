@@ -593,6 +593,54 @@ int cgks_step_info(cgks_solver* s, int* kernels_per_step)
     return CGKS_OK;
 }
 
+int cgks_profile_step(cgks_solver* s, double dt, float* ms, int* ids, int* n)
+{
+    if (!s || !ms || !ids || !n || *n < 1 || !(dt > 0.0) || !s->b->state_set) return CGKS_EINVAL;
+    cgks_batch* b = s->b;
+    cudaEvent_t ev[17];
+    int cap = std::min(*n, 16), cnt = 0, r = CGKS_OK;
+    for (int q = 0; q <= 16; ++q) CK(cudaEventCreate(&ev[q]));
+    CK(cudaMemcpyAsync(b->dfixed, &dt, 8, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaEventRecord(ev[0], b->stream));
+    auto rec = [&](int id) -> int {
+        if (cnt < cap) {
+            ids[cnt] = id;
+            if (cudaEventRecord(ev[cnt + 1], b->stream) != cudaSuccess) return CGKS_ECUDA;
+        }
+        ++cnt;
+        return CGKS_OK;
+    };
+    {
+        int use = 0;
+        const double* fx = b->dfixed;
+        Mesh* dm = b->dmesh;
+        int nn = b->n;
+        void* args[] = {&dm, &nn, &use, &fx};
+        CK(cudaLaunchKernel((const void*)k_dt<0>, dim3((nn + 127) / 128), dim3(128), args, 0, b->stream));
+        if ((r = rec(4))) goto done;
+    }
+    for (int stage = 1; stage <= 2; ++stage) {
+        if (b->dim == 2) {
+            if ((r = launch(b, (const void*)b->k.lines, W_LINES, 0, stage, true)) || (r = rec(10 * stage + 0))) goto done;
+        }
+        if ((r = launch(b, (const void*)b->k.normal, W_NORMAL, 1, stage, true)) || (r = rec(10 * stage + 1))) goto done;
+        if ((r = launch(b, (const void*)(stage == 1 ? b->k.flux1 : b->k.flux2), W_FLUX, stage == 1 ? 2 : 3, 0, false)) ||
+            (r = rec(10 * stage + 2))) goto done;
+        if ((r = launch(b, (const void*)(stage == 1 ? b->k.upd1 : b->k.upd2), W_CELLS, stage == 1 ? 4 : 5, 0, false)) ||
+            (r = rec(10 * stage + 3))) goto done;
+    }
+done:
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess && !r) r = CGKS_ECUDA;
+    if (!r) {
+        int m = std::min(cnt, cap);
+        for (int q = 0; q < m; ++q)
+            if (cudaEventElapsedTime(&ms[q], ev[q], ev[q + 1]) != cudaSuccess) r = CGKS_ECUDA;
+        *n = m;
+    }
+    for (int q = 0; q <= 16; ++q) cudaEventDestroy(ev[q]);
+    return r;
+}
+
 void cgks_destroy(cgks_solver* s)
 {
     if (!s) return;
