@@ -183,6 +183,41 @@ int cgks_batch_get_state(cgks_batch* b, int k, double* W, double* Wx, double* Wy
                          double* Wx_line, double* Wy_line);
 void cgks_batch_destroy(cgks_batch* b);
 
+/* ---------------------------------------------------------------- no-allocation step
+ * One S2O4 step of a 1-D mesh that allocates no device memory.  The paper has
+ * no counterpart: this exists for callers that cannot call cudaMalloc, for
+ * example code running under another framework's memory manager that owns
+ * the whole device (and forbids raw allocations), or code on a latency-bound
+ * path where an allocation (which may synchronise the device) is not allowed.
+ *
+ * All intermediate data (stage state, accumulator, face data, descriptors)
+ * lives in one file-scope device array of CGKS_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library keeps until process exit; meshes are limited to
+ * nx <= CGKS_NOALLOC_MAX_CELLS (larger nx returns CGKS_EINVAL).
+ *
+ * Arguments: p (dim must be 1; FIXED boundaries are not supported here and
+ * return CGKS_ENOTSUP), nx cells on [x0, x1]; device pointers state_in and
+ * state_out of 6*nx doubles ([W(3 vars)][nx] then [Wx(3 vars)][nx]; they may
+ * be equal), sigma_in (nx+1 doubles, or NULL: initialised from the cell
+ * averages as in cgks_set_state) and sigma_out (nx+1 doubles); dt > 0 fixed,
+ * dt <= 0 the CFL rule; status_out (device unsigned int, may be NULL)
+ * receives the step's status word (nonzero: non-physical state met).  The
+ * work is enqueued on `stream` (NULL: the legacy default stream) and the call
+ * returns without waiting.
+ *
+ * The first call on a device does its set-up there (finds the scratch array's
+ * device address, loads the reconstruction tables): make that first call
+ * before any stream capture.  Every call uses the same scratch array and
+ * clears the parts that must start at zero; calls that overlap on the GPU
+ * (different streams, or devices sharing nothing but this array's contents
+ * per device) race on it and must be serialised by the caller. */
+#define CGKS_NOALLOC_MAX_CELLS 4096
+#define CGKS_NOALLOC_SCRATCH_BYTES (4u << 20)
+int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, double x1,
+                         const double* state_in, const double* sigma_in,
+                         double* state_out, double* sigma_out, double dt,
+                         unsigned* status_out, void* stream);
+
 /* ---------------------------------------------------------------- host tables
  * The reconstruction functionals the kernels use, for inspection (no GPU
  * needed).  Stencil st: 0 S0, 1 S1, 2 S2, 3 r5, 4 r7, 5 r9 (Sec. 3.2); row:

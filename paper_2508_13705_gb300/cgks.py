@@ -27,7 +27,7 @@ EXPORTS = ("cgks_default_params", "cgks_init_mesh", "cgks_set_state", "cgks_set_
            "cgks_get_state", "cgks_get_state_device", "cgks_get_stats", "cgks_step_info",
            "cgks_destroy", "cgks_strerror", "cgks_batch_init", "cgks_batch_set_state",
            "cgks_batch_step", "cgks_batch_sync", "cgks_batch_get_state", "cgks_batch_destroy",
-           "cgks_stencil_row", "cgks_profile_step")
+           "cgks_stencil_row", "cgks_profile_step", "cgks_step_1d_noalloc")
 
 
 class Params(ctypes.Structure):
@@ -89,6 +89,8 @@ def lib():
         L.cgks_stencil_row.argtypes = [ip, ip, ip, dp]
         L.cgks_profile_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.cgks_step_1d_noalloc.argtypes = [ctypes.POINTER(Params), ip, ctypes.c_double, ctypes.c_double,
+                                           vp, vp, vp, vp, ctypes.c_double, vp, vp]
         _lib = L
     return _lib
 

@@ -729,3 +729,125 @@ int cgks_stencil_row(int order, int st, int row, double* out)
 }
 
 } // extern "C"
+
+// ---------------------------------------------------------------- no-allocation 1-D step
+//
+// For callers that may not allocate device memory: every buffer a 1-D step
+// needs besides the caller's state and sigma arrays lives in the file-scope
+// array below.  The existing kernels run unchanged; only their descriptor
+// points into this array.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CGKS_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+const int kMaxDevices = 64;
+unsigned char* g_noalloc_base[kMaxDevices];  // device address of the array, per device
+
+// Once per device, with that device current: the array's device address
+// (host code must not use the array's name as an address) and the tables.
+int noalloc_setup(int dev)
+{
+    if (dev < 0 || dev >= kMaxDevices) return CGKS_ENOTSUP;
+    if (g_noalloc_base[dev]) return CGKS_OK;
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return CGKS_ECUDA;
+    int r = load_tables();
+    if (r) return r;
+    g_noalloc_base[dev] = (unsigned char*)ptr;
+    return CGKS_OK;
+}
+
+} // namespace
+
+extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, double x1,
+                                    const double* state_in, const double* sigma_in,
+                                    double* state_out, double* sigma_out, double dt,
+                                    unsigned* status_out, void* stream)
+{
+    int r = validate(p);
+    if (r) return r;
+    if (p->dim != 1) return CGKS_EINVAL;
+    if (p->bc[0] == CGKS_BC_FIXED || p->bc[1] == CGKS_BC_FIXED) return CGKS_ENOTSUP;
+    if (nx < 1 || nx > CGKS_NOALLOC_MAX_CELLS || !(x1 > x0)) return CGKS_EINVAL;
+    if (!state_in || !state_out || !sigma_out) return CGKS_EINVAL;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if ((r = noalloc_setup(dev))) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t rs = p->precision == CGKS_FP64 ? 8 : 4;
+    // carve the array: S1, ACC, sigma (new), FR, FO, SP, scalars, descriptor, offsets
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align256(o + bytes); return at; };
+    size_t oS1 = take(6 * (size_t)nx * 8), oACC = take(6 * (size_t)nx * 8), oSN = take((size_t)(nx + 1) * 8);
+    size_t oFR = take(3 * (size_t)(nx + 1) * 24 * rs), oFO = take((size_t)(nx + 1) * 16 * rs);
+    size_t oSP = take((size_t)(nx + 1) * 8), oSC = take(512), oM = take(sizeof(Mesh));
+    size_t oOF = take(W_COUNT * 2 * sizeof(long long));
+    if (o > CGKS_NOALLOC_SCRATCH_BYTES) return CGKS_EINVAL;
+    unsigned char* base = g_noalloc_base[dev];
+    Mesh g;
+    std::memset(&g, 0, sizeof(g));
+    g.nx = nx; g.ny = 1; g.order = p->order; g.oi = (p->order - 5) / 2;
+    for (int q = 0; q < 4; ++q) g.bc[q] = p->bc[q];
+    g.tau_mode = p->tau_mode;
+    g.dx = (x1 - x0) / nx; g.dy = 1.0;
+    g.gamma = p->gamma; g.K = (3.0 - p->gamma) / (p->gamma - 1.0); g.thr = p->sigma_thres;
+    g.ghi = p->gamma_hi; g.glo = p->gamma_lo; g.eps = p->weno_eps; g.c1 = p->tau_c1; g.c2 = p->tau_c2;
+    g.cfl = p->cfl; g.plane = nx;
+    g.S0 = state_out;
+    g.S1 = (double*)(base + oS1);
+    g.ACC = (double*)(base + oACC);
+    g.sig_x = sigma_out;
+    g.sig_xn = (double*)(base + oSN);
+    g.FR[0] = base + oFR; g.FO[0] = base + oFO; g.SP[0] = (double*)(base + oSP);
+    unsigned char* sc = base + oSC;
+    g.dt = (double*)sc; g.t = (double*)(sc + 8); g.status = (unsigned*)(sc + 16);
+    g.bad = (long long*)(sc + 24); g.smax = (unsigned long long*)(sc + 32);
+    g.branch = (unsigned long long*)(sc + 40); g.ghost = (const double*)(sc + 80);
+    long long off[W_COUNT * 2];
+    for (int kind = 0; kind < W_COUNT; ++kind) { off[2 * kind] = 0; off[2 * kind + 1] = items(kind, 1, 1, nx, 1); }
+    Mesh* dmesh = (Mesh*)(base + oM);
+    long long* doff = (long long*)(base + oOF);
+    // scalars start from zero (bad index from its maximum); descriptor and offsets in
+    CK(cudaMemsetAsync(sc, 0, 512, st));
+    long long mx = LLONG_MAX;
+    CK(cudaMemcpyAsync(g.bad, &mx, 8, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(dmesh, &g, sizeof(Mesh), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(doff, off, sizeof(off), cudaMemcpyHostToDevice, st));
+    if (state_out != state_in) CK(cudaMemcpyAsync(state_out, state_in, 6 * (size_t)nx * 8, cudaMemcpyDeviceToDevice, st));
+    if (sigma_in && sigma_in != sigma_out)
+        CK(cudaMemcpyAsync(sigma_out, sigma_in, (size_t)(nx + 1) * 8, cudaMemcpyDeviceToDevice, st));
+    if (dt > 0.0) CK(cudaMemcpyAsync(g.dt + 0, &dt, 8, cudaMemcpyHostToDevice, st));
+    Kfns k = pick_kfns(1, p->order, p->precision);
+    int nsm = 1;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    auto go = [&](const void* fn, int kind, int stage, bool has_stage, int threads) -> int {
+        Work w;
+        w.mesh = dmesh;
+        w.off = doff + 2 * kind;
+        w.n = 1;
+        w.total = off[2 * kind + 1];
+        long long need = (w.total + threads - 1) / threads;
+        int grid = (int)std::max<long long>(1, std::min<long long>(need, 4LL * nsm));
+        void* a2[] = {&w, &stage};
+        void* a1[] = {&w};
+        CK(cudaLaunchKernel(fn, dim3(grid), dim3(threads), has_stage ? a2 : a1, 0, st));
+        return CGKS_OK;
+    };
+    if (!sigma_in && (r = go((const void*)k.siginit, W_SIGINIT, 0, false, 256))) return r;
+    // dt: the CFL reduction into the scratch scalars, or the fixed value copied above
+    int use_cfl = dt > 0.0 ? 0 : 1;
+    if (use_cfl && (r = go((const void*)k.cfl, W_CELLS, 0, false, 256))) return r;
+    {
+        int n1 = 1;
+        const double* fixed = g.dt;
+        void* args[] = {&dmesh, &n1, &use_cfl, &fixed};
+        CK(cudaLaunchKernel((const void*)k_dt<0>, dim3(1), dim3(32), args, 0, st));
+    }
+    for (int stage = 1; stage <= 2; ++stage) {
+        if ((r = go((const void*)k.normal, W_NORMAL, stage, true, 256))) return r;
+        if ((r = go((const void*)(stage == 1 ? k.flux1 : k.flux2), W_FLUX, 0, false, 128))) return r;
+        if ((r = go((const void*)(stage == 1 ? k.upd1 : k.upd2), W_CELLS, 0, false, 256))) return r;
+    }
+    if (status_out) CK(cudaMemcpyAsync(status_out, g.status, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
+    return CGKS_OK;
+}
