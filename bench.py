@@ -298,8 +298,15 @@ def main():
         pg.destroy_process_group()
 
 
-def accuracy(torch, cgks, order, stream, n=256, t_end=10.0):
-    """L1 density error of both forms at t = 10 (one period) on n^2 cells."""
+def accuracy(torch, cgks, order, stream, meshes=(64, 128, 256), t_end=10.0):
+    """L1 density error of both forms at t = 10 (one period) on several meshes;
+    reports the finest mesh where the FP32-bulk error is within 10% of FP64's."""
+    rows = [accuracy_one(torch, cgks, order, stream, n, t_end) for n in meshes]
+    ok = [r["mesh"][0] for r in rows if r["within_10pct"]]
+    return {"t": t_end, "rows": rows, "finest_mesh_within_10pct": max(ok) if ok else None}
+
+
+def accuracy_one(torch, cgks, order, stream, n, t_end):
     from paper_2508_13705_gb300 import inputs
     st = inputs.vortex_2d(n, order)
     out = {"mesh": [n, n], "t": t_end}

@@ -205,7 +205,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // per-mesh slab layout
 struct Layout {
-    size_t S, ACC, sigx, sigy, LA[2], FR[2], FO[2], SP[2], scal, total;
+    size_t S, F, ACC, sigx, sigy, LA[2], FR[2], FO[2], SP[2], AT[2], DN[2], scal, total;
 };
 
 Layout layout(int dim, int M, size_t rs, int nx, int ny)
@@ -216,6 +216,7 @@ Layout layout(int dim, int M, size_t rs, int nx, int ny)
     int nacc = dim == 2 ? 4 + 8 * M : 6;
     size_t o = 0;
     L.S = o; o = align256(o + 2 * np * plane * 8);
+    L.F = o; o = align256(o + (rs == 4 ? 2 * np * plane * 4 : 0));  // FP32-bulk float planes
     L.ACC = o; o = align256(o + nacc * plane * 8);
     L.sigx = o; o = align256(o + 2 * (size_t)(nx + 1) * ny * 8);
     L.sigy = o; o = align256(o + (dim == 2 ? 2 * (size_t)(ny + 1) * nx * 8 : 0));
@@ -226,6 +227,8 @@ Layout layout(int dim, int M, size_t rs, int nx, int ny)
         L.FR[d] = o; o = align256(o + (on ? (size_t)(nb + 2) * (na + 1) * M * 24 * rs : 0));
         L.FO[d] = o; o = align256(o + (on ? (size_t)nb * (na + 1) * M * 16 * rs : 0));
         L.SP[d] = o; o = align256(o + (on ? (size_t)nb * (na + 1) * M * 8 : 0));
+        L.AT[d] = o; o = align256(o + (on && dim == 2 ? (size_t)(nb + 2) * (na + 6) * rs : 0));
+        L.DN[d] = o; o = align256(o + (on && dim == 2 ? (size_t)(nb + 2) * (na + 6) * 4 * rs : 0));
     }
     L.scal = o; o = align256(o + 512);
     L.total = o;
@@ -290,6 +293,10 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         char* m0 = b->slab + base[k];
         g.S0 = (double*)(m0 + L[k].S);
         g.S1 = g.S0 + (size_t)b->nplanes * g.plane;
+        if (b->rsize == 4) {
+            g.F0 = (float*)(m0 + L[k].F);
+            g.F1 = g.F0 + (size_t)b->nplanes * g.plane;
+        }
         g.ACC = (double*)(m0 + L[k].ACC);
         g.sig_x = (double*)(m0 + L[k].sigx);
         g.sig_xn = g.sig_x + (size_t)(nx[k] + 1) * ny[k];
@@ -300,6 +307,8 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
             g.FR[d] = m0 + L[k].FR[d];
             g.FO[d] = m0 + L[k].FO[d];
             g.SP[d] = (double*)(m0 + L[k].SP[d]);
+            g.AT[d] = m0 + L[k].AT[d];
+            g.DN[d] = m0 + L[k].DN[d];
         }
         char* sc = m0 + L[k].scal;
         g.dt = (double*)sc;
@@ -399,9 +408,18 @@ int set_state_impl(cgks_batch* b, int k, const double* W, const double* Wx, cons
 
 // Run the per-mesh init kernels (sigma init when needed, positivity check)
 // over the whole table after a set_state.
+// FP32-bulk form: the float planes follow the FP64 state after a set (to_float)
+// and the FP64 slope planes follow the float planes before a read-out.
+int convert_state(cgks_batch* b, int to_float)
+{
+    if (b->rsize != 4) return CGKS_OK;
+    return launch(b, (const void*)b->k.convert, W_CELLS, 6, to_float, true);
+}
+
 int post_set(cgks_batch* b, bool init_sigma)
 {
     int r;
+    if ((r = convert_state(b, 1))) return r;
     if (init_sigma && (r = launch(b, (const void*)b->k.siginit, W_SIGINIT, 6, 0, false))) return r;
     if ((r = launch(b, (const void*)b->k.check, W_CELLS, 6, 0, false))) return r;
     CK(cudaStreamSynchronize(b->stream));
@@ -465,6 +483,7 @@ int cgks_set_state_device(cgks_solver* s, const double* W, const double* Wx, con
     int r = set_state_impl(s->b, 0, W, Wx, Wy, Wx_line, Wy_line, sigma_x, sigma_y, cudaMemcpyDeviceToDevice, false);
     if (r) return r;
     s->b->state_set = true;
+    if ((r = convert_state(s->b, 1))) return r;
     if (sigma_x == nullptr) return launch(s->b, (const void*)s->b->k.siginit, W_SIGINIT, 6, 0, false);
     return CGKS_OK;
 }
@@ -530,6 +549,10 @@ static int get_state_impl(cgks_batch* b, int k, double* W, double* Wx, double* W
     size_t P = (size_t)g.plane;
     int nv = b->nvar;
     cudaStream_t s = b->stream;
+    if (b->state_set) {
+        int r = convert_state(b, 0);
+        if (r) return r;
+    }
     if (W) CK(cudaMemcpyAsync(W, g.S0, nv * P * 8, kind, s));
     if (Wx) CK(cudaMemcpyAsync(Wx, g.S0 + nv * P, nv * P * 8, kind, s));
     if (b->dim == 2) {
@@ -782,6 +805,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     size_t oFR = take(3 * (size_t)(nx + 1) * 24 * rs), oFO = take((size_t)(nx + 1) * 16 * rs);
     size_t oSP = take((size_t)(nx + 1) * 8), oSC = take(512), oM = take(sizeof(Mesh));
     size_t oOF = take(W_COUNT * 2 * sizeof(long long));
+    size_t oF = take(rs == 4 ? 2 * 6 * (size_t)nx * 4 : 0);  // FP32-bulk float planes
     if (o > CGKS_NOALLOC_SCRATCH_BYTES) return CGKS_EINVAL;
     unsigned char* base = g_noalloc_base[dev];
     Mesh g;
@@ -795,6 +819,10 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     g.cfl = p->cfl; g.plane = nx;
     g.S0 = state_out;
     g.S1 = (double*)(base + oS1);
+    if (rs == 4) {
+        g.F0 = (float*)(base + oF);
+        g.F1 = g.F0 + 6 * (size_t)nx;
+    }
     g.ACC = (double*)(base + oACC);
     g.sig_x = sigma_out;
     g.sig_xn = (double*)(base + oSN);
@@ -833,6 +861,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
         CK(cudaLaunchKernel(fn, dim3(grid), dim3(threads), has_stage ? a2 : a1, 0, st));
         return CGKS_OK;
     };
+    if (rs == 4 && (r = go((const void*)k.convert, W_CELLS, 1, true, 256))) return r;
     if (!sigma_in && (r = go((const void*)k.siginit, W_SIGINIT, 0, false, 256))) return r;
     // dt: the CFL reduction into the scratch scalars, or the fixed value copied above
     int use_cfl = dt > 0.0 ? 0 : 1;
@@ -848,6 +877,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
         if ((r = go((const void*)(stage == 1 ? k.flux1 : k.flux2), W_FLUX, 0, false, 128))) return r;
         if ((r = go((const void*)(stage == 1 ? k.upd1 : k.upd2), W_CELLS, 0, false, 256))) return r;
     }
+    if (rs == 4 && (r = go((const void*)k.convert, W_CELLS, 0, true, 256))) return r;
     if (status_out) CK(cudaMemcpyAsync(status_out, g.status, sizeof(unsigned), cudaMemcpyDeviceToDevice, st));
     return CGKS_OK;
 }

@@ -67,11 +67,16 @@ struct Mesh {
     // state: planes of nx*ny doubles.  2-D: W[4] Wx[4] Wy[4] Wxl[m][4] Wyl[m][4];
     // 1-D: W[3] Wx[3]
     double *S0, *S1;                // S0: state n (and n+1), S1: stage-1 state W*
+    float *F0, *F1;                 // FP32-bulk form: float copies of all planes of S0 / S1
+                                    // (the FP64 planes hold the cell averages; their
+                                    // slope planes are rebuilt from these on read-out)
     double *ACC;                    // 2-D: W[4] Wxl[m][4] Wyl[m][4]; 1-D: W[3] Wface[3]
     double *sig_x, *sig_y;          // sigma of the previous step [ny][nx+1], [ny+1][nx]
     double *sig_xn, *sig_yn;        // sigma being built this step
     const double* ghost;            // 1-D fixed BC ghost cells
     void *LA[2], *FR[2], *FO[2];    // scratch per direction (R typed)
+    void* AT[2];                    // tangential r5 DFF per cell (R typed)
+    void* DN[2];                    // normal-direction DFF of each cell, packed [4] (R typed)
     double* SP[2];                  // sigma per face Gauss point
     double* dt;                     // device scalar (this mesh's step)
     double* t;                      // device scalar (simulated time)
@@ -103,9 +108,21 @@ __device__ __forceinline__ int imod(int a, int n) { int r = a % n; return r < 0 
 
 // ------------------------------------------------------------------ ghost cells
 
+// The state planes the bulk arithmetic reads: FP64 planes for R = double,
+// the float copies for R = float.  which: 0 state n, 1 stage-1 state.
+template <typename R> __device__ __forceinline__ const R* state_planes(const Mesh& g, int which);
+template <> __device__ __forceinline__ const double* state_planes<double>(const Mesh& g, int which)
+{
+    return which == 0 ? g.S0 : g.S1;
+}
+template <> __device__ __forceinline__ const float* state_planes<float>(const Mesh& g, int which)
+{
+    return which == 0 ? g.F0 : g.F1;
+}
+
 // kind: 0 W, 1 Wx, 2 Wy, 3 Wx_line, 4 Wy_line (global orientation)
-template <int D, int M>
-__device__ __forceinline__ double cell(const Mesh& g, const double* S, int kind, int v, int l, int i, int j)
+template <int D, int M, typename T>
+__device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, int l, int i, int j)
 {
     bool zero = false;
     if (i < 0 || i >= g.nx) {
@@ -115,7 +132,7 @@ __device__ __forceinline__ double cell(const Mesh& g, const double* S, int kind,
             i = imod(i, g.nx);
         } else if (bc == BC_FIXED) {
             int layer = side == 0 ? (-1 - i) : (i - g.nx);
-            return g.ghost[((side * 3 + layer) * 2 + (kind == 0 ? 0 : 1)) * 3 + v];
+            return (T)g.ghost[((side * 3 + layer) * 2 + (kind == 0 ? 0 : 1)) * 3 + v];
         } else {
             i = i < 0 ? 0 : g.nx - 1;
             zero = (kind == 1 || kind == 3);
@@ -129,7 +146,7 @@ __device__ __forceinline__ double cell(const Mesh& g, const double* S, int kind,
             zero = zero || (kind == 2 || kind == 4);
         }
     }
-    if (zero) return 0.0;
+    if (zero) return (T)0;
     long long idx = (long long)j * g.nx + i;
     int p;
     if (D == 1) {
@@ -170,6 +187,27 @@ __device__ __forceinline__ double sigy(const Mesh& g, const double* sy, int i, i
     return sy[(long long)f * g.nx + i];
 }
 
+// 16-byte vector moves of 4 consecutive values (float4, or two double2)
+__device__ __forceinline__ void ld4(const float* p, float v[4])
+{
+    float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void ld4(const double* p, double v[4])
+{
+    double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+__device__ __forceinline__ void st4(float* p, const float v[4])
+{
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const double v[4])
+{
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+
 // ------------------------------------------------------------------ ASE-DFF
 
 // Branch and stencil DFFs of one cell from the sigma of the six faces
@@ -185,18 +223,42 @@ __device__ __forceinline__ double dff_alpha(double A, double thr) { return A < t
 
 __device__ __forceinline__ Dff dff_select(int order, const double s[6], double thr)
 {
+    // The threshold tests come first; a DFF below 1 (a division) is formed
+    // only on the HWENO-AO branch, where the sub-stencil DFFs are used.  On
+    // every linear branch the chosen stencil's DFF is 1 by construction.
     Dff d;
     double A_r5 = s[1] + s[2] + s[3] + s[4];
     double A_r7 = s[0] + A_r5 + s[5];
-    d.a[0] = dff_alpha(s[1] + s[2] + s[3], thr);
-    d.a[1] = dff_alpha(s[2] + s[3] + s[4], thr);
-    d.a[2] = dff_alpha(A_r5, thr);
-    d.a[3] = d.a[2];
-    double a7 = dff_alpha(A_r7, thr), a9 = dff_alpha(2.0 * A_r7, thr);
-    if (d.a[3] < 1.0) { d.st = -1; d.alpha = d.a[3]; }
-    else if (order == 5 || a7 < 1.0) { d.st = ST_R5; d.alpha = d.a[3]; }
-    else if (order == 7 || a9 < 1.0) { d.st = ST_R7; d.alpha = a7; }
-    else { d.st = ST_R9; d.alpha = a9; }
+    d.a[0] = d.a[1] = d.a[2] = d.a[3] = 1.0;
+    d.alpha = 1.0;
+    if (A_r5 >= thr) {
+        d.st = -1;
+        d.a[0] = dff_alpha(s[1] + s[2] + s[3], thr);
+        d.a[1] = dff_alpha(s[2] + s[3] + s[4], thr);
+        d.a[2] = d.a[3] = d.alpha = thr / A_r5;
+    } else if (order == 5 || A_r7 >= thr) {
+        d.st = ST_R5;
+    } else if (order == 7 || 2.0 * A_r7 >= thr) {
+        d.st = ST_R7;
+    } else {
+        d.st = ST_R9;
+    }
+    return d;
+}
+
+// Packed form of a Dff for a per-cell buffer: (a0, a1, a3, stencil code)
+template <typename R>
+__device__ __forceinline__ void dff_pack(const Dff& d, R out[4])
+{
+    out[0] = (R)d.a[0]; out[1] = (R)d.a[1]; out[2] = (R)d.a[3]; out[3] = (R)d.st;
+}
+template <typename R>
+__device__ __forceinline__ Dff dff_unpack(const R in[4])
+{
+    Dff d;
+    d.a[0] = (double)in[0]; d.a[1] = (double)in[1]; d.a[2] = d.a[3] = (double)in[2];
+    d.st = (int)in[3];
+    d.alpha = d.st < 0 ? d.a[3] : 1.0;
     return d;
 }
 

@@ -13,6 +13,8 @@
 //                                     side 1 = right (from cell f); W, W_n, W_nn
 //   FO  [nb][na+1][M][16]             per-point stage outputs (global frame)
 //   SP  [nb][na+1][M]                 sigma per face Gauss point (Eq. 3.2)
+//   AT  [nb+2][na+6]                  tangential r5 DFF of each cell (Step 3)
+//   DN  [nb+2][na+6][4]               normal-direction DFF of each cell (Step 2), packed
 #pragma once
 #include "cgks_device.cuh"
 
@@ -28,8 +30,8 @@ __device__ __forceinline__ void local_dims(const Mesh& g, int dir, int& na, int&
 }
 
 // cell value in local coordinates; lkind: 0 W, 1 W_n (cell), 2 W_t (cell), 3 W_n line
-template <int D, int M>
-__device__ __forceinline__ double lcell(const Mesh& g, const double* S, int dir, int lkind, int v, int l, int a, int b)
+template <int D, int M, typename T>
+__device__ __forceinline__ T lcell(const Mesh& g, const T* S, int dir, int lkind, int v, int l, int a, int b)
 {
     int kind;
     if (lkind == 0) kind = 0;
@@ -37,7 +39,7 @@ __device__ __forceinline__ double lcell(const Mesh& g, const double* S, int dir,
     else if (lkind == 2) kind = dir == 0 ? 2 : 1;
     else kind = dir == 0 ? 3 : 4;
     int i = dir == 0 ? a : b, j = dir == 0 ? b : a;
-    return cell<D, M>(g, S, kind, vglob(dir, v), l, i, j);
+    return cell<D, M, T>(g, S, kind, vglob(dir, v), l, i, j);
 }
 
 // sigma of normal faces (f, b) and of tangential faces of column a (a, f)
@@ -73,30 +75,63 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         local_dims<M>(g, dir, na, nb);
         int a = (int)(li % (na + 6)) - 3;
         int b = (int)(li / (na + 6)) - 1;
-        const double* S = stage == 1 ? g.S0 : g.S1;
+        const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
         double s6[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) s6[q] = lsigT(g, g.sig_x, g.sig_y, dir, a, b - 2 + q);
         Dff dff = dff_select(g.order, s6, g.thr);
-        double ht = dir == 0 ? g.dy : g.dx;
+        R ht = (R)(dir == 0 ? g.dy : g.dx);
         int rows[M];
 #pragma unroll
         for (int l = 0; l < M; ++l) rows[l] = 6 + l;
-        R* LA = (R*)g.LA[dir] + (((long long)(b + 1) * (na + 6) + (a + 3)) * M) * 4;
-#pragma unroll 1
-        for (int v = 0; v < 4; ++v) {
-            double qi = lcell<2, M>(g, S, dir, 0, v, 0, a, b);
-            R dp[10];
+        long long cidx = (long long)(b + 1) * (na + 6) + (a + 3);
+        R* LA = (R*)g.LA[dir] + cidx * M * 4;
+        // tangential r5 DFF of this cell, reused by Step 3 in k_flux
+        ((R*)g.AT[dir])[cidx] = (R)dff.a[3];
+        // normal-direction DFF of this cell, reused by every Gauss line in k_normal
+        if (a >= -1 && a <= na) {
+            double n6[6];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                dp[q] = (R)(lcell<2, M>(g, S, dir, 0, v, 0, a, b + q - 2) - qi);
-                dp[5 + q] = (R)(ht * lcell<2, M>(g, S, dir, 2, v, 0, a, b + q - 2));
+            for (int q = 0; q < 6; ++q) n6[q] = lsigN<2>(g, g.sig_x, g.sig_y, dir, a - 2 + q, b);
+            R pk[4];
+            dff_pack<R>(dff_select(g.order, n6, g.thr), pk);
+            st4((R*)g.DN[dir] + cidx * 4, pk);
+        }
+        // the tangential stencil: a direct walk for interior cells
+        bool inner = a >= 0 && a < na && b >= 2 && b + 2 < nb;
+        long long P = g.plane;
+        long long ci = dir == 0 ? (long long)b * g.nx + a : (long long)a * g.nx + b;
+        long long st = dir == 0 ? g.nx : 1;  // tangential neighbour stride
+        int pt = dir == 0 ? 8 : 4;           // plane of the tangential cell slope
+        R res[M][4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            int gv = vglob(dir, v);
+            R qi, dp[10];
+            if (inner) {
+                const R* w0 = S + gv * P + ci;
+                const R* wt = S + (pt + gv) * P + ci;
+                qi = w0[0];
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    dp[q] = w0[(q - 2) * st] - qi;
+                    dp[5 + q] = ht * wt[(q - 2) * st];
+                }
+            } else {
+                qi = lcell<2, M, R>(g, S, dir, 0, v, 0, a, b);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    dp[q] = lcell<2, M, R>(g, S, dir, 0, v, 0, a, b + q - 2) - qi;
+                    dp[5 + q] = ht * lcell<2, M, R>(g, S, dir, 2, v, 0, a, b + q - 2);
+                }
             }
             R out[M];
             recon<R, M>(dff, g.oi, rows, 0, dp, out, g.ghi, g.glo, g.eps);
 #pragma unroll
-            for (int l = 0; l < M; ++l) LA[l * 4 + v] = (R)(qi + (double)out[l]);
+            for (int l = 0; l < M; ++l) res[l][v] = qi + out[l];
         }
+#pragma unroll
+        for (int l = 0; l < M; ++l) st4(LA + l * 4, res[l]);
     }
 }
 
@@ -108,6 +143,7 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
     __shared__ unsigned long long cnt[4];
     if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
     __syncthreads();
+    constexpr int NV = D + 2;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
          gi += (long long)gridDim.x * blockDim.x) {
         int k = find_mesh(w, gi);
@@ -124,58 +160,84 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         long long r = D == 2 ? li / M : li;
         int a = (int)(r % (na + 2)) - 1;
         int b = D == 2 ? (int)(r / (na + 2)) - 1 : 0;
-        const double* S = stage == 1 ? g.S0 : g.S1;
-        double s6[6];
+        const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
+        Dff dff;
+        if (D == 2) {
+            R pk[4];
+            ld4((const R*)g.DN[dir] + ((long long)(b + 1) * (na + 6) + (a + 3)) * 4, pk);
+            dff = dff_unpack<R>(pk);
+        } else {
+            double s6[6];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) s6[q] = D == 2 ? lsigN<2>(g, g.sig_x, g.sig_y, dir, a - 2 + q, b)
-                                                   : sigx<1>(g, g.sig_x, a - 2 + q, 0);
-        Dff dff = dff_select(g.order, s6, g.thr);
+            for (int q = 0; q < 6; ++q) s6[q] = sigx<1>(g, g.sig_x, a - 2 + q, 0);
+            dff = dff_select(g.order, s6, g.thr);
+        }
         {
             int bi = dff.st < 0 ? 0 : dff.st - ST_R5 + 1;
             atomicAdd(&cnt[bi], 1ull);
         }
-        double hn = dir == 0 ? g.dx : g.dy;
+        R hn = (R)(dir == 0 ? g.dx : g.dy);
         const int rows[6] = {0, 1, 2, 3, 4, 5};
-        const R* LA = D == 2 ? (const R*)g.LA[dir] : nullptr;
         R* FR = (R*)g.FR[dir];
-        constexpr int NV = D + 2;
-#pragma unroll 1
+        // the line averages of the five stencil cells on this Gauss line
+        R la5[5][4];
+        if (D == 2) {
+            const R* la = (const R*)g.LA[dir] + ((long long)(b + 1) * (na + 6) + (a + 3)) * M * 4 + l * 4;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) ld4(la + (q - 2) * M * 4, la5[q]);
+        }
+        R sideL[3][4], sideR[3][4];
+        // the normal stencil of line slopes: a direct walk for interior cells
+        bool inner = D == 2 && a >= 2 && a + 2 < na && b >= 0 && b < nb;
+        long long P = g.plane;
+        long long ci = dir == 0 ? (long long)b * g.nx + a : (long long)a * g.nx + b;
+        long long sn = dir == 0 ? 1 : g.nx;                    // normal neighbour stride
+        int pl0 = (dir == 0 ? 12 : 12 + 4 * M) + 4 * l;         // first line-slope plane of line l
+#pragma unroll
         for (int v = 0; v < NV; ++v) {
-            double qi;
+            R qi;
             R dp[10];
             if (D == 2) {
-                const R* la = LA + ((long long)(b + 1) * (na + 6) + (a + 3)) * M * 4 + l * 4 + v;
-                qi = (double)la[0];
+                qi = la5[2][v];
 #pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    dp[q] = (R)((double)la[(q - 2) * M * 4] - qi);
-                    dp[5 + q] = (R)(hn * lcell<2, M>(g, S, dir, 3, v, l, a + q - 2, b));
+                for (int q = 0; q < 5; ++q) dp[q] = la5[q][v] - qi;
+                if (inner) {
+                    const R* ws = S + (pl0 + vglob(dir, v)) * P + ci;
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) dp[5 + q] = hn * ws[(q - 2) * sn];
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) dp[5 + q] = hn * lcell<2, M, R>(g, S, dir, 3, v, l, a + q - 2, b);
                 }
             } else {
-                qi = cell<1, 1>(g, S, 0, v, 0, a, 0);
+                qi = cell<1, 1, R>(g, S, 0, v, 0, a, 0);
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
-                    dp[q] = (R)(cell<1, 1>(g, S, 0, v, 0, a + q - 2, 0) - qi);
-                    dp[5 + q] = (R)(hn * cell<1, 1>(g, S, 1, v, 0, a + q - 2, 0));
+                    dp[q] = cell<1, 1, R>(g, S, 0, v, 0, a + q - 2, 0) - qi;
+                    dp[5 + q] = hn * cell<1, 1, R>(g, S, 1, v, 0, a + q - 2, 0);
                 }
             }
             R out[6];
             recon<R, 6>(dff, g.oi, rows, 0, dp, out, g.ghi, g.glo, g.eps);
-            R ih = (R)(1.0 / hn);
-            // side 0: left state of face a+1 (value at xi = +1/2)
-            if (a + 1 <= na) {
-                R* fr = FR + ((((long long)(b + 1) * (na + 1) + (a + 1)) * M + l) * 2 + 0) * 3 * 4;
-                fr[0 * 4 + v] = (R)(qi + (double)out[0]);
-                fr[1 * 4 + v] = out[1] * ih;
-                fr[2 * 4 + v] = out[2] * ih * ih;
-            }
-            // side 1: right state of face a (value at xi = -1/2)
-            if (a >= 0) {
-                R* fr = FR + ((((long long)(b + 1) * (na + 1) + a) * M + l) * 2 + 1) * 3 * 4;
-                fr[0 * 4 + v] = (R)(qi + (double)out[3]);
-                fr[1 * 4 + v] = out[4] * ih;
-                fr[2 * 4 + v] = out[5] * ih * ih;
-            }
+            R ih = (R)1 / hn;
+            sideL[0][v] = qi + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
+            sideR[0][v] = qi + out[3]; sideR[1][v] = out[4] * ih; sideR[2][v] = out[5] * ih * ih;
+        }
+        if (D == 1) {
+#pragma unroll
+            for (int nd = 0; nd < 3; ++nd) { sideL[nd][3] = (R)0; sideR[nd][3] = (R)0; }
+        }
+        // side 0: left state of face a+1 (value at xi = +1/2)
+        if (a + 1 <= na) {
+            R* fr = FR + ((((long long)(b + 1) * (na + 1) + (a + 1)) * M + l) * 2 + 0) * 12;
+#pragma unroll
+            for (int nd = 0; nd < 3; ++nd) st4(fr + nd * 4, sideL[nd]);
+        }
+        // side 1: right state of face a (value at xi = -1/2)
+        if (a >= 0) {
+            R* fr = FR + ((((long long)(b + 1) * (na + 1) + a) * M + l) * 2 + 1) * 12;
+#pragma unroll
+            for (int nd = 0; nd < 3; ++nd) st4(fr + nd * 4, sideR[nd]);
         }
     }
     __syncthreads();
@@ -209,34 +271,31 @@ __global__ void __launch_bounds__(128) k_flux(Work w)
         for (int side = 0; side < 2; ++side) {
             const R* fr = FR + ((((long long)(b + 1) * (na + 1) + f) * M + l) * 2 + side) * 12;
 #pragma unroll
-            for (int nd = 0; nd < 3; ++nd)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) sd[side].d[nd][v] = v < NV ? fr[nd * 4 + v] : (R)0;
+            for (int nd = 0; nd < 3; ++nd) ld4(fr + nd * 4, sd[side].d[nd]);
             if (D == 2) {
                 // Step 3: tangential derivatives from the 3M face points of
                 // segments b-1, b, b+1, scaled by the tangential r5 DFF of the
                 // reconstructing cell (a = f-1 for the left state, f for the right)
                 int a = side == 0 ? f - 1 : f;
-                double s6[6];
-#pragma unroll
-                for (int q = 0; q < 6; ++q) s6[q] = lsigT(g, g.sig_x, g.sig_y, dir, a, b - 2 + q);
-                double at = dff_alpha(s6[1] + s6[2] + s6[3] + s6[4], g.thr);
-                double ht = dir == 0 ? g.dy : g.dx;
+                R at = ((const R*)g.AT[dir])[(long long)(b + 1) * (na + 6) + (a + 3)];
+                R iht = (R)1 / (R)(dir == 0 ? g.dy : g.dx);
                 const auto& T = Tab<R>::get(g.oi);
-                R c1 = (R)(at / ht), c2 = (R)(at / (ht * ht));
+                R c1 = at * iht, c2 = at * iht * iht;
                 R wt[4] = {0, 0, 0, 0}, wtt[4] = {0, 0, 0, 0}, wnt[4] = {0, 0, 0, 0};
 #pragma unroll
                 for (int s = 0; s < 3; ++s)
 #pragma unroll
                     for (int kk = 0; kk < M; ++kk) {
                         const R* q = FR + ((((long long)(b + s) * (na + 1) + f) * M + kk) * 2 + side) * 12;
+                        R x0[4], x1[4];
+                        ld4(q, x0);
+                        ld4(q + 4, x1);
                         R w1 = T.d1[l][s * M + kk], w2 = T.d2[l][s * M + kk];
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
-                            R x0 = q[v], x1 = q[4 + v];
-                            wt[v] += w1 * x0;
-                            wtt[v] += w2 * x0;
-                            wnt[v] += w1 * x1;
+                            wt[v] += w1 * x0[v];
+                            wtt[v] += w2 * x0[v];
+                            wnt[v] += w1 * x1[v];
                         }
                     }
 #pragma unroll
@@ -247,44 +306,53 @@ __global__ void __launch_bounds__(128) k_flux(Work w)
                 }
             }
         }
-        // Eq. 3.2 sigma and positivity of the reconstructed states in FP64
-        double pz[2], mn[2], mt[2];
+        // Eq. 3.2 sigma and the positivity test of the reconstructed states,
+        // evaluated in the precision the states carry (the face means, stencil
+        // sums and branch thresholds that use sigma are FP64)
+        R pz[2], mn[2], mt[2];
         bool bad = false;
+        const R gm = (R)g.gamma;
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-            double rho = (double)sd[side].d[0][0];
-            double un = (double)sd[side].d[0][1] / rho;
-            double ut = D == 2 ? (double)sd[side].d[0][2] / rho : 0.0;
-            double p = (g.gamma - 1.0) * ((double)sd[side].d[0][NV - 1] - 0.5 * rho * (un * un + ut * ut));
-            double c = sqrt(g.gamma * p / rho);
-            pz[side] = p; mn[side] = un / c; mt[side] = ut / c;
-            bad |= !(rho > 0.0) || !(p > 0.0);
+            R rho = sd[side].d[0][0];
+            R ir = (R)1 / rho;
+            R un = sd[side].d[0][1] * ir;
+            R ut = D == 2 ? sd[side].d[0][2] * ir : (R)0;
+            R p = (gm - (R)1) * (sd[side].d[0][NV - 1] - (R)0.5 * rho * (un * un + ut * ut));
+            R ic = (R)1 / sqrt(gm * p * ir);
+            pz[side] = p; mn[side] = un * ic; mt[side] = ut * ic;
+            bad |= !(rho > (R)0) || !(p > (R)0);
         }
-        double dpz = fabs(pz[0] - pz[1]);
-        double sig = dpz / pz[0] + dpz / pz[1] + (mn[0] - mn[1]) * (mn[0] - mn[1]) + (mt[0] - mt[1]) * (mt[0] - mt[1]);
+        R dpz = fabs(pz[0] - pz[1]);
+        double sig = (double)(dpz / pz[0] + dpz / pz[1] + (mn[0] - mn[1]) * (mn[0] - mn[1]) + (mt[0] - mt[1]) * (mt[0] - mt[1]));
         double dt = *g.dt;
         R F[4], Ft[4], Q0[4], Wt[4], Wtt[4];
         bool ok = kinetic<R, D>(sd[0], sd[1], (R)g.gamma, (R)g.K, g.tau_mode, (R)g.c1, (R)g.c2, (R)dt, F, Ft, Q0, Wt, Wtt);
         long long pt = (((long long)b * (na + 1) + f) * M + l);
         R* FO = (R*)g.FO[dir] + pt * 16;
         R Dt = (R)dt;
-        bool finite = true;
+        R o[4][4];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
+        for (int v = 0; v < 4; ++v) {
             int gv = D == 2 ? vglob(dir, v) : v;
+            if (v >= NV) { o[0][v] = o[1][v] = o[2][v] = o[3][v] = (R)0; continue; }
             if (STAGE == 1) {
-                R o0 = (R)0.5 * Dt * F[v] + (R)0.125 * Dt * Dt * Ft[v];
-                R o1 = Dt * F[v] + Dt * Dt / (R)6 * Ft[v];
-                R o2 = Q0[v] + (R)0.5 * Dt * Wt[v] + (R)0.125 * Dt * Dt * Wtt[v];
-                R o3 = Q0[v] + Dt * Wt[v] + Dt * Dt / (R)6 * Wtt[v];
-                FO[0 * 4 + gv] = o0; FO[1 * 4 + gv] = o1; FO[2 * 4 + gv] = o2; FO[3 * 4 + gv] = o3;
-                finite &= isfinite((double)o0) && isfinite((double)o1) && isfinite((double)o2) && isfinite((double)o3);
+                o[0][gv] = (R)0.5 * Dt * F[v] + (R)0.125 * Dt * Dt * Ft[v];
+                o[1][gv] = Dt * F[v] + Dt * Dt / (R)6 * Ft[v];
+                o[2][gv] = Q0[v] + (R)0.5 * Dt * Wt[v] + (R)0.125 * Dt * Dt * Wtt[v];
+                o[3][gv] = Q0[v] + Dt * Wt[v] + Dt * Dt / (R)6 * Wtt[v];
             } else {
-                R o0 = Dt * Dt / (R)3 * Ft[v];
-                R o1 = Dt * Dt / (R)3 * Wtt[v];
-                FO[0 * 4 + gv] = o0; FO[1 * 4 + gv] = o1;
-                finite &= isfinite((double)o0) && isfinite((double)o1);
+                o[0][gv] = Dt * Dt / (R)3 * Ft[v];
+                o[1][gv] = Dt * Dt / (R)3 * Wtt[v];
             }
+        }
+        bool finite = true;
+        constexpr int NO = STAGE == 1 ? 4 : 2;
+#pragma unroll
+        for (int q = 0; q < NO; ++q) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) finite &= isfinite(o[q][v]);
+            st4(FO + q * 4, o[q]);
         }
         if (STAGE == 1) g.SP[dir][pt] = sig;
         if (bad || !ok || !finite) flag_bad(g, pt);
@@ -292,9 +360,13 @@ __global__ void __launch_bounds__(128) k_flux(Work w)
 }
 
 // -------------------------------------------------------------- update (2-D)
+// Stage 1 writes W* (S1) and the accumulator; stage 2 writes state n+1 (S0).
+// FP32-bulk form: the FP64 planes receive the cell averages, the float planes
+// (F1 / F0) everything the next stage reads.
 template <int M, typename R, int STAGE>
 __global__ void __launch_bounds__(256) k_update2(Work w)
 {
+    constexpr bool BULK32 = sizeof(R) == 4;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
          gi += (long long)gridDim.x * blockDim.x) {
         int k = find_mesh(w, gi);
@@ -312,50 +384,74 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
         double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
         long long P = g.plane;
         double* out = STAGE == 1 ? g.S1 : g.S0;
-        const double* Sin = g.S0;
-        bool bad = false;
+        float* outf = STAGE == 1 ? g.F1 : g.F0;
+        double fx0[4] = {0, 0, 0, 0}, fy0[4] = {0, 0, 0, 0}, fx1[4] = {0, 0, 0, 0}, fy1[4] = {0, 0, 0, 0};
+        double sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
 #pragma unroll 1
-        for (int v = 0; v < 4; ++v) {
-            double fx0 = 0, fy0 = 0, fx1 = 0, fy1 = 0;
-            double sx = 0, sy = 0;
+        for (int l = 0; l < M; ++l) {
+            double wl = T.gw[l];
+            R a[4], bq[4], cq[4], dq[4];
+            // stage 1: o0 = F(dt/2), o1 = dt F + dt^2/6 F_t, o2 = W(dt/2), o3 = W0 + dt W_t + dt^2/6 W_tt
+            // stage 2: o0 = dt^2/3 F_t*, o1 = dt^2/3 W_tt*
 #pragma unroll
-            for (int l = 0; l < M; ++l) {
-                double wl = T.gw[l];
-                fx0 += wl * ((double)xr[l * 16 + v] - (double)xl[l * 16 + v]);
-                fy0 += wl * ((double)yr[l * 16 + v] - (double)yl[l * 16 + v]);
-                if (STAGE == 1) {
-                    fx1 += wl * ((double)xr[l * 16 + 4 + v] - (double)xl[l * 16 + 4 + v]);
-                    fy1 += wl * ((double)yr[l * 16 + 4 + v] - (double)yl[l * 16 + 4 + v]);
-                    double lx = ((double)xr[l * 16 + 8 + v] - (double)xl[l * 16 + 8 + v]) * idx;
-                    double ly = ((double)yr[l * 16 + 8 + v] - (double)yl[l * 16 + 8 + v]) * idy;
-                    out[(12 + 4 * l + v) * P + c] = lx;
-                    out[(12 + 4 * M + 4 * l + v) * P + c] = ly;
-                    sx += wl * lx;
-                    sy += wl * ly;
-                    g.ACC[(4 + 4 * l + v) * P + c] = ((double)xr[l * 16 + 12 + v] - (double)xl[l * 16 + 12 + v]) * idx;
-                    g.ACC[(4 + 4 * M + 4 * l + v) * P + c] = ((double)yr[l * 16 + 12 + v] - (double)yl[l * 16 + 12 + v]) * idy;
-                } else {
-                    double lx = g.ACC[(4 + 4 * l + v) * P + c] + ((double)xr[l * 16 + 4 + v] - (double)xl[l * 16 + 4 + v]) * idx;
-                    double ly = g.ACC[(4 + 4 * M + 4 * l + v) * P + c] + ((double)yr[l * 16 + 4 + v] - (double)yl[l * 16 + 4 + v]) * idy;
-                    out[(12 + 4 * l + v) * P + c] = lx;
-                    out[(12 + 4 * M + 4 * l + v) * P + c] = ly;
-                    sx += wl * lx;
-                    sy += wl * ly;
+            for (int q = 0; q < (STAGE == 1 ? 4 : 2); ++q) {
+                ld4(xr + l * 16 + q * 4, a);
+                ld4(xl + l * 16 + q * 4, bq);
+                ld4(yr + l * 16 + q * 4, cq);
+                ld4(yl + l * 16 + q * 4, dq);
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    double dx_ = (double)a[v] - (double)bq[v];
+                    double dy_ = (double)cq[v] - (double)dq[v];
+                    if (q == 0) {
+                        fx0[v] += wl * dx_;
+                        fy0[v] += wl * dy_;
+                    } else if (STAGE == 1 && q == 1) {
+                        fx1[v] += wl * dx_;
+                        fy1[v] += wl * dy_;
+                    } else if ((STAGE == 1 && q == 2) || (STAGE == 2 && q == 1)) {
+                        double lx = dx_ * idx, ly = dy_ * idy;
+                        if (STAGE == 2) {
+                            lx += g.ACC[(4 + 4 * l + v) * P + c];
+                            ly += g.ACC[(4 + 4 * M + 4 * l + v) * P + c];
+                        }
+                        if (BULK32) {
+                            outf[(12 + 4 * l + v) * P + c] = (float)lx;
+                            outf[(12 + 4 * M + 4 * l + v) * P + c] = (float)ly;
+                        } else {
+                            out[(12 + 4 * l + v) * P + c] = lx;
+                            out[(12 + 4 * M + 4 * l + v) * P + c] = ly;
+                        }
+                        sx[v] += wl * lx;
+                        sy[v] += wl * ly;
+                    } else {  // stage 1, q == 3: line-slope part of the accumulator
+                        g.ACC[(4 + 4 * l + v) * P + c] = dx_ * idx;
+                        g.ACC[(4 + 4 * M + 4 * l + v) * P + c] = dy_ * idy;
+                    }
                 }
             }
+        }
+        bool bad = false;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            double Wn;
             if (STAGE == 1) {
-                double W = Sin[v * P + c];
-                double Ws = W - fx0 * idx - fy0 * idy;   // Eq. 2.21
-                out[v * P + c] = Ws;
-                g.ACC[v * P + c] = W - fx1 * idx - fy1 * idy;
-                bad |= !isfinite(Ws);
+                double W = g.S0[v * P + c];
+                Wn = W - fx0[v] * idx - fy0[v] * idy;               // Eq. 2.21
+                g.ACC[v * P + c] = W - fx1[v] * idx - fy1[v] * idy;
             } else {
-                double Wn = g.ACC[v * P + c] - fx0 * idx - fy0 * idy;  // Eq. 2.22-2.23
-                out[v * P + c] = Wn;
-                bad |= !isfinite(Wn);
+                Wn = g.ACC[v * P + c] - fx0[v] * idx - fy0[v] * idy;  // Eq. 2.22-2.23
             }
-            out[(4 + v) * P + c] = sx;   // cell slopes: Gauss sum of the line slopes
-            out[(8 + v) * P + c] = sy;
+            out[v * P + c] = Wn;
+            bad |= !isfinite(Wn);
+            if (BULK32) {
+                outf[v * P + c] = (float)Wn;
+                outf[(4 + v) * P + c] = (float)sx[v];  // cell slopes: Gauss sum of the line slopes
+                outf[(8 + v) * P + c] = (float)sy[v];
+            } else {
+                out[(4 + v) * P + c] = sx[v];
+                out[(8 + v) * P + c] = sy[v];
+            }
         }
         // face sigma of this step (Eq. 3.1): mean over the face's Gauss points
         if (STAGE == 1) {
@@ -391,6 +487,7 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
 template <typename R, int STAGE>
 __global__ void __launch_bounds__(256) k_update1(Work w)
 {
+    constexpr bool BULK32 = sizeof(R) == 4;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
          gi += (long long)gridDim.x * blockDim.x) {
         int k = find_mesh(w, gi);
@@ -403,20 +500,27 @@ __global__ void __launch_bounds__(256) k_update1(Work w)
         long long P = g.plane;
         bool bad = false;
         for (int v = 0; v < 3; ++v) {
+            double Wn, Sn;
             if (STAGE == 1) {
                 double W = g.S0[v * P + i];
-                double Ws = W - ((double)xr[v] - (double)xl[v]) * idx;
-                g.S1[v * P + i] = Ws;
-                g.S1[(3 + v) * P + i] = ((double)xr[8 + v] - (double)xl[8 + v]) * idx;
+                Wn = W - ((double)xr[v] - (double)xl[v]) * idx;
+                Sn = ((double)xr[8 + v] - (double)xl[8 + v]) * idx;
+                g.S1[v * P + i] = Wn;
                 g.ACC[v * P + i] = W - ((double)xr[4 + v] - (double)xl[4 + v]) * idx;
                 g.ACC[(3 + v) * P + i] = ((double)xr[12 + v] - (double)xl[12 + v]) * idx;
-                bad |= !isfinite(Ws);
             } else {
-                double Wn = g.ACC[v * P + i] - ((double)xr[v] - (double)xl[v]) * idx;
+                Wn = g.ACC[v * P + i] - ((double)xr[v] - (double)xl[v]) * idx;
+                Sn = g.ACC[(3 + v) * P + i] + ((double)xr[4 + v] - (double)xl[4 + v]) * idx;
                 g.S0[v * P + i] = Wn;
-                g.S0[(3 + v) * P + i] = g.ACC[(3 + v) * P + i] + ((double)xr[4 + v] - (double)xl[4 + v]) * idx;
-                bad |= !isfinite(Wn);
             }
+            if (BULK32) {
+                float* outf = STAGE == 1 ? g.F1 : g.F0;
+                outf[v * P + i] = (float)Wn;
+                outf[(3 + v) * P + i] = (float)Sn;
+            } else {
+                (STAGE == 1 ? g.S1 : g.S0)[(3 + v) * P + i] = Sn;
+            }
+            bad |= !isfinite(Wn);
         }
         if (STAGE == 1) {
             g.sig_xn[i] = g.SP[0][i];
@@ -426,6 +530,29 @@ __global__ void __launch_bounds__(256) k_update1(Work w)
             if (i == g.nx - 1) g.sig_x[g.nx] = g.sig_xn[g.nx];
         }
         if (bad) flag_bad(g, i);
+    }
+}
+
+// -------------------------------------------------------------- FP32-bulk state copies
+// to_float: all FP64 planes of state n -> the float planes (after a state is set);
+// otherwise the float slope planes -> the FP64 planes (before a state is read
+// out; the FP64 cell averages are already current).
+template <int D, int M>
+__global__ void __launch_bounds__(256) k_convert(Work w, int to_float)
+{
+    constexpr int NP = D == 2 ? 12 + 8 * M : 6;
+    constexpr int NV = D + 2;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
+         gi += (long long)gridDim.x * blockDim.x) {
+        int k = find_mesh(w, gi);
+        const Mesh& g = w.mesh[k];
+        long long c = gi - w.off[k];
+        long long P = g.plane;
+        if (to_float) {
+            for (int p = 0; p < NP; ++p) g.F0[p * P + c] = (float)g.S0[p * P + c];
+        } else {
+            for (int p = NV; p < NP; ++p) g.S0[p * P + c] = (double)g.F0[p * P + c];
+        }
     }
 }
 
@@ -510,7 +637,7 @@ __global__ void k_sigma_init(Work w)
         for (int s = 0; s < 2; ++s)
             for (int v = 0; v < D + 2; ++v) {
                 int a = f - 1 + s;
-                Ws[s][v] = dir == 0 ? cell<D, 4>(g, g.S0, 0, v, 0, a, b) : cell<D, 4>(g, g.S0, 0, v, 0, b, a);
+                Ws[s][v] = dir == 0 ? cell<D, 4, double>(g, g.S0, 0, v, 0, a, b) : cell<D, 4, double>(g, g.S0, 0, v, 0, b, a);
             }
         double pz[2], mn[2], mt[2];
         for (int s = 0; s < 2; ++s) {

@@ -26,6 +26,7 @@ Kfns make_kfns()
     k.cfl = k_cfl<D>;
     k.siginit = k_sigma_init<D>;
     k.check = k_check_state<D>;
+    k.convert = k_convert<D, M>;
     k.upload = upload_tables;
     return k;
 }

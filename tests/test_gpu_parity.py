@@ -248,3 +248,68 @@ def test_step_before_state_is_an_error():
     with pytest.raises(cgks.CgksError) as e:
         s.step(1e-3)
     assert e.value.code == cgks.EINVAL
+
+
+# ---------------------------------------------------------------- FP32-bulk form
+
+def test_fp32_bulk_2d_error_vs_oracle():
+    """FP32-bulk form against the FP64 oracle: the difference is FP32 rounding
+    (~1e-7 per step), far below the discretisation error of these meshes."""
+    n = 32
+    st = inputs.vortex_2d(n, 9)
+    s = cgks.Solver(2, 9, n, n, extent=(0, 10, 0, 10), precision=cgks.FP32_BULK)
+    o = oracle.Oracle(2, 9, n, n, extent=(0, 10, 0, 10))
+    s.set_state(*st)
+    o.set_state(*st)
+    for _ in range(10):
+        dt = o.compute_dt()
+        s.step(dt)
+        o.step(dt)
+    s.sync()
+    g = s.get_state()
+    assert rel_l1(g["W"], o.W) < 2e-7
+    assert rel_l1(g["Wx_line"], o.Wxl) < 1e-4
+
+
+def test_fp32_bulk_keeps_design_order_1d():
+    """Density wave, order 5: FP32-bulk errors equal the FP64 ones within 1%
+    while the discretisation error (>= 1e-6) dominates the FP32 rounding
+    (~1e-7 after a few hundred steps), so the design order holds."""
+    errs = {}
+    for prec in (cgks.FP64, cgks.FP32_BULK):
+        e = []
+        for N in (10, 20):
+            dx = 2.0 / N
+            dt = 0.3 * dx ** (5 / 4)
+            s = cgks.Solver(1, 5, N, extent=(0, 2, 0, 1), precision=prec)
+            s.set_state(*inputs.density_wave_1d(N))
+            t = 0.0
+            while t < 2.0 - 1e-12:
+                d = min(dt, 2.0 - t)
+                s.step(d)
+                t += d
+            s.sync()
+            e.append(np.abs(s.get_state()["W"][0, 0] - inputs.density_wave_1d_exact_avg(N, 2.0)).mean())
+        errs[prec] = e
+    for a, b in zip(errs[cgks.FP32_BULK], errs[cgks.FP64]):
+        assert abs(a / b - 1) < 0.01
+    assert abs(np.log2(errs[cgks.FP32_BULK][0] / errs[cgks.FP32_BULK][1]) - 5) < 0.2
+
+
+def test_fp32_bulk_quadrants_per_step():
+    """Shock case in FP32 bulk: per-step difference to the oracle stays at FP32
+    rounding level and the step flags nothing."""
+    n = 16
+    st = inputs.quadrants_2d(n, 9, seed=0)
+    kw = dict(tau_mode=cgks.TAU_HGKS, bc=(1, 1, 1, 1))
+    o = oracle.Oracle(2, 9, n, n, extent=(0, 1, 0, 1), **kw)
+    o.set_state(*st)
+    s = cgks.Solver(2, 9, n, n, extent=(0, 1, 0, 1), precision=cgks.FP32_BULK, **kw)
+    for k in range(3):
+        g0 = o.get_state()
+        s.set_state(g0["W"], g0["Wx"], g0["Wy"], g0["Wx_line"], g0["Wy_line"], g0["sigma_x"], g0["sigma_y"])
+        dt = o.compute_dt()
+        s.step(dt)
+        s.sync()
+        o.step(dt)
+        assert rel_l1(s.get_state()["W"], o.W) < 1e-6
