@@ -7,7 +7,8 @@
 // Momentum components are ordered normal first in the local frame.
 //
 // Scratch layouts per mesh and direction (na, nb: cells along / across the
-// normal; M Gauss points per face):
+// normal; M Gauss points per face).  Direction 0 as written; direction 1 with
+// the two spatial indices swapped, so the global x index is always fastest:
 //   LA  [nb+2][na+6][M][4]            line averages, b in [-1, nb], a in [-3, na+2]
 //   FR  [nb+2][na+1][M][2][3][4]      face states: side 0 = left (from cell f-1),
 //                                     side 1 = right (from cell f); W, W_n, W_nn
@@ -53,6 +54,26 @@ __device__ __forceinline__ double lsigT(const Mesh& g, const double* sx, const d
     return dir == 0 ? sigy(g, sy, a, f) : sigx<2>(g, sx, f, a);
 }
 
+// Scratch indexing.  Direction 0 keeps the normal index a (= i) fastest,
+// direction 1 the tangential index b (= i): in both directions the global x
+// index runs fastest, in memory and across threads, so every kernel walks the
+// SoA state planes with unit stride.
+//   cell_idx: a in [-3, na+2], b in [-1, nb]   (LA, AT, DN)
+//   fr_row:   bb = b + 1 in [0, nb+1], f in [0, na]   (FR)
+//   pt_idx:   b in [0, nb), f in [0, na]       (FO, SP)
+__device__ __forceinline__ long long cell_idx(int dir, int na, int nb, int a, int b)
+{
+    return dir == 0 ? (long long)(b + 1) * (na + 6) + (a + 3) : (long long)(a + 3) * (nb + 2) + (b + 1);
+}
+__device__ __forceinline__ long long fr_row(int dir, int na, int nb, int bb, int f)
+{
+    return dir == 0 ? (long long)bb * (na + 1) + f : (long long)f * (nb + 2) + bb;
+}
+__device__ __forceinline__ long long pt_idx(int dir, int na, int nb, int b, int f)
+{
+    return dir == 0 ? (long long)b * (na + 1) + f : (long long)f * nb + b;
+}
+
 __device__ __forceinline__ void flag_bad(const Mesh& g, long long idx)
 {
     atomicOr(g.status, STATUS_NONPHYS);
@@ -73,8 +94,9 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         if (dir == 1) li -= nxl;
         int na, nb;
         local_dims<M>(g, dir, na, nb);
-        int a = (int)(li % (na + 6)) - 3;
-        int b = (int)(li / (na + 6)) - 1;
+        int a, b;
+        if (dir == 0) { a = (int)(li % (na + 6)) - 3; b = (int)(li / (na + 6)) - 1; }
+        else { b = (int)(li % (nb + 2)) - 1; a = (int)(li / (nb + 2)) - 3; }
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
         double s6[6];
 #pragma unroll
@@ -84,7 +106,7 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         int rows[M];
 #pragma unroll
         for (int l = 0; l < M; ++l) rows[l] = 6 + l;
-        long long cidx = (long long)(b + 1) * (na + 6) + (a + 3);
+        long long cidx = cell_idx(dir, na, nb, a, b);
         R* LA = (R*)g.LA[dir] + cidx * M * 4;
         // tangential r5 DFF of this cell, reused by Step 3 in k_flux
         ((R*)g.AT[dir])[cidx] = (R)dff.a[3];
@@ -158,13 +180,16 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         }
         int l = D == 2 ? (int)(li % M) : 0;
         long long r = D == 2 ? li / M : li;
-        int a = (int)(r % (na + 2)) - 1;
-        int b = D == 2 ? (int)(r / (na + 2)) - 1 : 0;
+        int a, b;
+        if (dir == 0) { a = (int)(r % (na + 2)) - 1; b = D == 2 ? (int)(r / (na + 2)) - 1 : 0; }
+        else { b = (int)(r % (nb + 2)) - 1; a = (int)(r / (nb + 2)) - 1; }
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
+        long long cidx = cell_idx(dir, na, nb, a, b);
+        long long lstr = dir == 0 ? 1 : (nb + 2);  // LA stride between normal neighbours
         Dff dff;
         if (D == 2) {
             R pk[4];
-            ld4((const R*)g.DN[dir] + ((long long)(b + 1) * (na + 6) + (a + 3)) * 4, pk);
+            ld4((const R*)g.DN[dir] + cidx * 4, pk);
             dff = dff_unpack<R>(pk);
         } else {
             double s6[6];
@@ -182,9 +207,9 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         // the line averages of the five stencil cells on this Gauss line
         R la5[5][4];
         if (D == 2) {
-            const R* la = (const R*)g.LA[dir] + ((long long)(b + 1) * (na + 6) + (a + 3)) * M * 4 + l * 4;
+            const R* la = (const R*)g.LA[dir] + cidx * M * 4 + l * 4;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) ld4(la + (q - 2) * M * 4, la5[q]);
+            for (int q = 0; q < 5; ++q) ld4(la + (q - 2) * lstr * M * 4, la5[q]);
         }
         R sideL[3][4], sideR[3][4];
         // the normal stencil of line slopes: a direct walk for interior cells
@@ -229,13 +254,13 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         }
         // side 0: left state of face a+1 (value at xi = +1/2)
         if (a + 1 <= na) {
-            R* fr = FR + ((((long long)(b + 1) * (na + 1) + (a + 1)) * M + l) * 2 + 0) * 12;
+            R* fr = FR + ((fr_row(dir, na, nb, b + 1, a + 1) * M + l) * 2 + 0) * 12;
 #pragma unroll
             for (int nd = 0; nd < 3; ++nd) st4(fr + nd * 4, sideL[nd]);
         }
         // side 1: right state of face a (value at xi = -1/2)
         if (a >= 0) {
-            R* fr = FR + ((((long long)(b + 1) * (na + 1) + a) * M + l) * 2 + 1) * 12;
+            R* fr = FR + ((fr_row(dir, na, nb, b + 1, a) * M + l) * 2 + 1) * 12;
 #pragma unroll
             for (int nd = 0; nd < 3; ++nd) st4(fr + nd * 4, sideR[nd]);
         }
@@ -263,13 +288,14 @@ __global__ void __launch_bounds__(128) k_flux(Work w)
         }
         int l = D == 2 ? (int)(li % M) : 0;
         long long r = D == 2 ? li / M : li;
-        int f = (int)(r % (na + 1));
-        int b = D == 2 ? (int)(r / (na + 1)) : 0;
+        int f, b;
+        if (dir == 0) { f = (int)(r % (na + 1)); b = D == 2 ? (int)(r / (na + 1)) : 0; }
+        else { b = (int)(r % nb); f = (int)(r / nb); }
         const R* FR = (const R*)g.FR[dir];
         SideData<R, D> sd[2];
 #pragma unroll
         for (int side = 0; side < 2; ++side) {
-            const R* fr = FR + ((((long long)(b + 1) * (na + 1) + f) * M + l) * 2 + side) * 12;
+            const R* fr = FR + ((fr_row(dir, na, nb, b + 1, f) * M + l) * 2 + side) * 12;
 #pragma unroll
             for (int nd = 0; nd < 3; ++nd) ld4(fr + nd * 4, sd[side].d[nd]);
             if (D == 2) {
@@ -277,7 +303,7 @@ __global__ void __launch_bounds__(128) k_flux(Work w)
                 // segments b-1, b, b+1, scaled by the tangential r5 DFF of the
                 // reconstructing cell (a = f-1 for the left state, f for the right)
                 int a = side == 0 ? f - 1 : f;
-                R at = ((const R*)g.AT[dir])[(long long)(b + 1) * (na + 6) + (a + 3)];
+                R at = ((const R*)g.AT[dir])[cell_idx(dir, na, nb, a, b)];
                 R iht = (R)1 / (R)(dir == 0 ? g.dy : g.dx);
                 const auto& T = Tab<R>::get(g.oi);
                 R c1 = at * iht, c2 = at * iht * iht;
@@ -286,7 +312,7 @@ __global__ void __launch_bounds__(128) k_flux(Work w)
                 for (int s = 0; s < 3; ++s)
 #pragma unroll
                     for (int kk = 0; kk < M; ++kk) {
-                        const R* q = FR + ((((long long)(b + s) * (na + 1) + f) * M + kk) * 2 + side) * 12;
+                        const R* q = FR + ((fr_row(dir, na, nb, b + s, f) * M + kk) * 2 + side) * 12;
                         R x0[4], x1[4];
                         ld4(q, x0);
                         ld4(q + 4, x1);
@@ -328,7 +354,7 @@ __global__ void __launch_bounds__(128) k_flux(Work w)
         double dt = *g.dt;
         R F[4], Ft[4], Q0[4], Wt[4], Wtt[4];
         bool ok = kinetic<R, D>(sd[0], sd[1], (R)g.gamma, (R)g.K, g.tau_mode, (R)g.c1, (R)g.c2, (R)dt, F, Ft, Q0, Wt, Wtt);
-        long long pt = (((long long)b * (na + 1) + f) * M + l);
+        long long pt = pt_idx(dir, na, nb, b, f) * M + l;
         R* FO = (R*)g.FO[dir] + pt * 16;
         R Dt = (R)dt;
         R o[4][4];
@@ -379,8 +405,8 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
         // x-faces: b = j, f = i and i+1; y-faces: b = i, f = j and j+1
         const R* xl = FX + (((long long)j * (g.nx + 1) + i) * M) * 16;
         const R* xr = xl + M * 16;
-        const R* yl = FY + (((long long)i * (g.ny + 1) + j) * M) * 16;
-        const R* yr = yl + M * 16;
+        const R* yl = FY + (((long long)j * g.nx + i) * M) * 16;
+        const R* yr = yl + (long long)g.nx * M * 16;
         double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
         long long P = g.plane;
         double* out = STAGE == 1 ? g.S1 : g.S0;
@@ -466,11 +492,11 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
                 g.sig_xn[(long long)j * (g.nx + 1) + g.nx] = s / M;
             }
             s = 0;
-            for (int l = 0; l < M; ++l) s += SY[((long long)i * (g.ny + 1) + j) * M + l];
+            for (int l = 0; l < M; ++l) s += SY[((long long)j * g.nx + i) * M + l];
             g.sig_yn[(long long)j * g.nx + i] = s / M;
             if (j == g.ny - 1) {
                 s = 0;
-                for (int l = 0; l < M; ++l) s += SY[((long long)i * (g.ny + 1) + g.ny) * M + l];
+                for (int l = 0; l < M; ++l) s += SY[((long long)g.ny * g.nx + i) * M + l];
                 g.sig_yn[(long long)g.ny * g.nx + i] = s / M;
             }
         } else {
