@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--order", type=int, default=9)
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     return ap.parse_args()
 
 
@@ -288,6 +289,8 @@ def main():
     }
     if rank == 0 and not a.no_accuracy:
         line["accuracy"] = accuracy(torch, cgks, order, stream)
+    if rank == 0 and not a.no_batch:
+        line["batch"] = batch_bench(torch, cgks, stream)
     if rank == 0 and not a.no_cpu:
         rate, cores, el = cpu_oracle_rate(order, 128, 2)
         line["cpu_baseline"] = {"value": round(rate, 5), "unit": "Mcell-stage/s", "cores": cores, "kind": "oracle",
@@ -329,6 +332,64 @@ def accuracy_one(torch, cgks, order, stream, n, t_end):
     out["fp32_over_fp64"] = out["l1_fp32"] / out["l1_fp64"]
     out["within_10pct"] = out["fp32_over_fp64"] <= 1.10
     return out
+
+
+def batch_bench(torch, cgks, stream, count=256, order=7, steps=10):
+    """Config C5: 256 seeded uneven periodic meshes (sides 64-512, smooth modes
+    plus a planar shock), order 7, HGKS tau.  FP32-bulk batch (one persistent
+    launch per kernel, one graph per step, device CFL per instance) against
+    the same instances stepped one at a time in FP64."""
+    from paper_2508_13705_gb300 import inputs
+    sp = inputs.batch_specs(count, seed=0)
+    t0 = time.perf_counter()
+    states = [inputs.batch_instance(s, order, nq=2) for s in sp]
+    t_in = time.perf_counter() - t0
+    nx = [s["nx"] for s in sp]
+    ny = [s["ny"] for s in sp]
+    ext = [(0.0, 1.0, 0.0, s["ny"] / s["nx"]) for s in sp]
+    cells = sum(x * y for x, y in zip(nx, ny))
+    b = cgks.Batch(order, nx, ny, ext, precision=cgks.FP32_BULK, tau_mode=cgks.TAU_HGKS, stream=stream.cuda_stream)
+    for k, st in enumerate(states):
+        b.set_state(k, *st)
+    for _ in range(2):
+        b.step(None)
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        b.step(None)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms32 = e0.elapsed_time(e1)
+    rc = 0
+    try:
+        b.sync()
+    except cgks.CgksError as e:
+        rc = e.code
+    b.close()
+    # FP64, one instance at a time
+    k64 = 2
+    ms64 = 0.0
+    for k, st in enumerate(states):
+        s = cgks.Solver(2, order, nx[k], ny[k], extent=ext[k], precision=cgks.FP64, tau_mode=cgks.TAU_HGKS,
+                        stream=stream.cuda_stream)
+        s.set_state(*st)
+        s.advance(1, 0.0)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s.advance(k64, 0.0)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 += e0.elapsed_time(e1)
+        s.close()
+    return {"workload": "%d periodic instances, sides 64-512 (seed 0), Fourier modes + Mach 1.5-3 planar shock, "
+                        "order %d, HGKS tau, CFL 0.5" % (count, order),
+            "cells": cells, "fp32_batched": {"value": round(cells * 2 * steps / (ms32 / 1e3) / 1e6, 3),
+                                             "unit": "Mcell-stage/s", "steps": steps, "status": rc},
+            "fp64_one_at_a_time": {"value": round(cells * 2 * k64 / (ms64 / 1e3) / 1e6, 3),
+                                   "unit": "Mcell-stage/s", "steps": k64},
+            "input_gen_s": round(t_in, 1)}
 
 
 def reference_arm(a):

@@ -81,6 +81,7 @@ struct cgks_batch {
     std::vector<Mesh> host;      // host copy of the descriptors
     Mesh* dmesh = nullptr;       // device descriptors
     long long* doff = nullptr;   // device prefix arrays [W_COUNT][n+1]
+    long long* doff1 = nullptr;  // per-mesh single-mesh tables [n][W_COUNT][2] = {0, items}
     std::vector<long long> off;  // host prefix arrays
     double* dfixed = nullptr;    // fixed dt per mesh
     char* slab = nullptr;
@@ -330,6 +331,14 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         if (cudaMalloc(&b->doff, b->off.size() * sizeof(long long)) != cudaSuccess) { rr = CGKS_ENOMEM; break; }
         if (cudaMemcpy(b->dmesh, b->host.data(), n * sizeof(Mesh), cudaMemcpyHostToDevice) != cudaSuccess) { rr = CGKS_ECUDA; break; }
         if (cudaMemcpy(b->doff, b->off.data(), b->off.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess) { rr = CGKS_ECUDA; break; }
+        {
+            std::vector<long long> one((size_t)n * W_COUNT * 2, 0);
+            for (int k = 0; k < n; ++k)
+                for (int kind = 0; kind < W_COUNT; ++kind)
+                    one[((size_t)k * W_COUNT + kind) * 2 + 1] = items(kind, p->dim, b->M, nx[k], ny[k]);
+            if (cudaMalloc(&b->doff1, one.size() * sizeof(long long)) != cudaSuccess) { rr = CGKS_ENOMEM; break; }
+            if (cudaMemcpy(b->doff1, one.data(), one.size() * sizeof(long long), cudaMemcpyHostToDevice) != cudaSuccess) { rr = CGKS_ECUDA; break; }
+        }
         // zero the scalars and scratch once (bad index = max)
         if (cudaMemsetAsync(b->slab, 0, total, b->stream) != cudaSuccess) { rr = CGKS_ECUDA; break; }
         for (int k = 0; k < n; ++k) {
@@ -408,6 +417,37 @@ int set_state_impl(cgks_batch* b, int k, const double* W, const double* Wx, cons
 
 // Run the per-mesh init kernels (sigma init when needed, positivity check)
 // over the whole table after a set_state.
+// Launch a per-mesh kernel over the items of mesh k alone.
+int launch_one(cgks_batch* b, int k, const void* fn, int kind, int arg, bool has_arg)
+{
+    Work w;
+    w.mesh = b->dmesh + k;
+    w.off = b->doff1 + ((size_t)k * W_COUNT + kind) * 2;
+    w.n = 1;
+    w.total = items(kind, b->dim, b->M, b->host[k].nx, b->host[k].ny);
+    if (w.total == 0) return CGKS_OK;
+    int threads = 256;
+    long long need = (w.total + threads - 1) / threads;
+    int grid = (int)std::max<long long>(1, std::min<long long>(need, (long long)b->grid[6]));
+    void* a2[] = {&w, &arg};
+    void* a1[] = {&w};
+    CK(cudaLaunchKernel(fn, dim3(grid), dim3(threads), has_arg ? a2 : a1, 0, b->stream));
+    return CGKS_OK;
+}
+
+// After mesh k of a batch is set: its float planes, sigma and positivity check.
+int post_set_one(cgks_batch* b, int k)
+{
+    int r;
+    if (b->rsize == 4 && (r = launch_one(b, k, (const void*)b->k.convert, W_CELLS, 1, true))) return r;
+    if ((r = launch_one(b, k, (const void*)b->k.siginit, W_SIGINIT, 0, false))) return r;
+    if ((r = launch_one(b, k, (const void*)b->k.check, W_CELLS, 0, false))) return r;
+    CK(cudaStreamSynchronize(b->stream));
+    unsigned st = 0;
+    CK(cudaMemcpy(&st, b->host[k].status, 4, cudaMemcpyDeviceToHost));
+    return (st & STATUS_NONPHYS) ? CGKS_ENONPHYS : CGKS_OK;
+}
+
 // FP32-bulk form: the float planes follow the FP64 state after a set (to_float)
 // and the FP64 slope planes follow the float planes before a read-out.
 int convert_state(cgks_batch* b, int to_float)
@@ -698,11 +738,8 @@ int cgks_batch_set_state(cgks_batch* b, int k, const double* W, const double* Wx
     if (!b) return CGKS_EINVAL;
     int r = set_state_impl(b, k, W, Wx, Wy, Wx_line, Wy_line, nullptr, nullptr, cudaMemcpyHostToDevice, true);
     if (r) return r;
-    // sigma of every instance is (re)initialised from its cell averages; the
-    // table-wide init kernel also covers meshes set earlier, which is harmless
-    // before the first step and is why instances are set before stepping.
     b->state_set = true;
-    return post_set(b, true);
+    return post_set_one(b, k);
 }
 
 int cgks_batch_step(cgks_batch* b, const double* dt)
@@ -736,6 +773,7 @@ void cgks_batch_destroy(cgks_batch* b)
         if (b->gexec[q]) cudaGraphExecDestroy(b->gexec[q]);
     if (b->dmesh) cudaFree(b->dmesh);
     if (b->doff) cudaFree(b->doff);
+    if (b->doff1) cudaFree(b->doff1);
     if (b->slab) cudaFree(b->slab);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
     delete b;

@@ -254,7 +254,7 @@ def batch_specs(count=256, seed=0, lo=64, hi=512):
     return specs
 
 
-def batch_instance(spec, order, gamma=1.4):
+def batch_instance(spec, order, gamma=1.4, nq=4):
     """One batch member: smooth density modes on rho = 1, p = 1 plus a planar shock.
 
     The domain is [0,1] x [0, ny/nx] (square cells), periodic.  The shock front
@@ -280,7 +280,7 @@ def batch_instance(spec, order, gamma=1.4):
         p = np.where(post, p2, 1.0)
         return (rho, un, 0 * x, p) if ax == 0 else (rho, 0 * x, un, p)
 
-    W, Wx, Wy, Wxl, Wyl = cell_state_2d(prim, nx, ny, (0.0, 1.0, 0.0, Ly), order, gamma, nq=4)
+    W, Wx, Wy, Wxl, Wyl = cell_state_2d(prim, nx, ny, (0.0, 1.0, 0.0, Ly), order, gamma, nq=nq)
     # cells behind the front are uniform; the front sits on a face
     coord = (np.arange(ncell) + 0.5) * h
     post = coord < xs

@@ -31,18 +31,32 @@ def rel_l1(a, b):
     return np.abs(a - b).sum() / (den if den > 0 else 1.0)
 
 
+def slope_floor(orc):
+    """Rounding floor of a slope field: slopes are differences of interface
+    states divided by the cell size, and the oracle forms W_t, W_tt by the fit
+    of Eq. 2.29, which leaves a few ulps of the state in them.  Floor per value:
+    64 ulp of the largest state magnitude over the smallest cell size."""
+    h = min(orc.dx, orc.dy) if orc.dim == 2 else orc.dx
+    return 64 * np.finfo(float).eps * np.abs(orc.W).max() / h
+
+
 def compare(gpu, orc, fields, tol=TOL, what=""):
-    """State fields: relative L1.  sigma (Eq. 3.2) of smooth data is a
-    difference of nearly equal pressures (~1e-11), so it is compared
-    elementwise with an absolute floor of 1e-14 on top of the relative bound."""
+    """Cell averages: relative L1 <= tol.  Slope fields: relative L1 <= tol
+    on top of the rounding floor of slope_floor() per value.  sigma (Eq. 3.2)
+    of smooth data is a difference of nearly equal pressures (~1e-11), so it
+    is compared elementwise with an absolute floor of 1e-14."""
     o = orc.get_state()
     for f in fields:
         if f.startswith("sigma"):
             err = np.abs(gpu[f] - o[f]) - tol * np.abs(o[f])
             assert err.max() <= 1e-14, "%s %s: max excess %.3e" % (what, f, err.max())
-        else:
+        elif f == "W":
             e = rel_l1(gpu[f], o[f])
             assert e <= tol, "%s %s: rel L1 %.3e" % (what, f, e)
+        else:
+            d = np.abs(gpu[f] - o[f]).sum()
+            bound = tol * np.abs(o[f]).sum() + o[f].size * slope_floor(orc)
+            assert d <= bound, "%s %s: L1 diff %.3e > %.3e" % (what, f, d, bound)
 
 
 def run_both(dim, order, n, st, steps, extent, dt=None, ny=None, **kw):
