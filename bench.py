@@ -191,6 +191,9 @@ def main():
 
     # ---------------- FP32-bulk form (headline)
     s32 = run_gpu_form(torch, cgks, st, n, order, cgks.FP32_BULK, a.steps, a.warmup, stream)
+    tuned32 = s32.autotune()
+    s32.advance(1, 0.0)
+    s32.sync()
     kps = s32.kernels_per_step()
     clk = ClockSampler(local)
     clk.start()
@@ -211,6 +214,7 @@ def main():
     # ---------------- FP64 plain form, same mesh
     k64 = max(2, a.steps // 5)
     s64 = run_gpu_form(torch, cgks, st, n, order, cgks.FP64, k64, 1, stream)
+    tuned64 = s64.autotune()
     barrier(pg)
     torch.cuda.synchronize()
     e0.record(stream)
@@ -284,6 +288,7 @@ def main():
         "e2e": {"value": round(e2e_v, 3), "unit": "Mcell-stage/s", "h2d_bytes_per_step": bytes_state,
                 "d2h_bytes_per_step": bytes_state, "steps": k_e2e},
         "gpu_launches": kps * a.steps,
+        "autotuned_threads": {"fp32": tuned32, "fp64": tuned64},
         "status": rc32,
         "input_gen_s": round(t_in, 2),
     }
@@ -351,6 +356,7 @@ def batch_bench(torch, cgks, stream, count=256, order=7, steps=10):
     b = cgks.Batch(order, nx, ny, ext, precision=cgks.FP32_BULK, tau_mode=cgks.TAU_HGKS, stream=stream.cuda_stream)
     for k, st in enumerate(states):
         b.set_state(k, *st)
+    tuned = b.autotune()
     for _ in range(2):
         b.step(None)
     b.sync()
@@ -386,7 +392,8 @@ def batch_bench(torch, cgks, stream, count=256, order=7, steps=10):
     return {"workload": "%d periodic instances, sides 64-512 (seed 0), Fourier modes + Mach 1.5-3 planar shock, "
                         "order %d, HGKS tau, CFL 0.5" % (count, order),
             "cells": cells, "fp32_batched": {"value": round(cells * 2 * steps / (ms32 / 1e3) / 1e6, 3),
-                                             "unit": "Mcell-stage/s", "steps": steps, "status": rc},
+                                             "unit": "Mcell-stage/s", "steps": steps, "status": rc,
+                                             "autotuned_threads": tuned},
             "fp64_one_at_a_time": {"value": round(cells * 2 * k64 / (ms64 / 1e3) / 1e6, 3),
                                    "unit": "Mcell-stage/s", "steps": k64},
             "input_gen_s": round(t_in, 1)}

@@ -151,6 +151,17 @@ int cgks_get_state_device(cgks_solver* s, double* W, double* Wx, double* Wy, dou
 /* Diagnostics (synchronous). */
 int cgks_get_stats(cgks_solver* s, cgks_stats* st);
 
+/* Autotuner: times every stage kernel on the solver's current state at each
+ * admissible block size (64..512 threads, persistent grid = SM count x
+ * resident blocks) and keeps the fastest; the step graph is rebuilt on the
+ * next step.  The state is not advanced (only scratch is written; the
+ * simulated time is restored) and results do not depend on the choice: every
+ * work item is computed by one thread.  threads_out (may be NULL) receives
+ * the block sizes of lines, normal, flux (stage 1, 2), update (stage 1, 2).
+ * Requires a state (CGKS_EINVAL otherwise). */
+int cgks_autotune(cgks_solver* s, int* threads_out);
+int cgks_batch_autotune(cgks_batch* b, int* threads_out);
+
 /* Number of graph nodes (kernel launches) one CFL step makes. */
 int cgks_step_info(cgks_solver* s, int* kernels_per_step);
 

@@ -27,7 +27,8 @@ EXPORTS = ("cgks_default_params", "cgks_init_mesh", "cgks_set_state", "cgks_set_
            "cgks_get_state", "cgks_get_state_device", "cgks_get_stats", "cgks_step_info",
            "cgks_destroy", "cgks_strerror", "cgks_batch_init", "cgks_batch_set_state",
            "cgks_batch_step", "cgks_batch_sync", "cgks_batch_get_state", "cgks_batch_destroy",
-           "cgks_stencil_row", "cgks_profile_step", "cgks_step_1d_noalloc")
+           "cgks_stencil_row", "cgks_profile_step", "cgks_step_1d_noalloc", "cgks_autotune",
+           "cgks_batch_autotune")
 
 
 class Params(ctypes.Structure):
@@ -89,6 +90,8 @@ def lib():
         L.cgks_stencil_row.argtypes = [ip, ip, ip, dp]
         L.cgks_profile_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(ctypes.c_float),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+        L.cgks_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.cgks_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.cgks_step_1d_noalloc.argtypes = [ctypes.POINTER(Params), ip, ctypes.c_double, ctypes.c_double,
                                            vp, vp, vp, vp, ctypes.c_double, vp, vp]
         _lib = L
@@ -216,6 +219,12 @@ class Solver:
         return dict(t=s.t, min_rho=s.min_rho, min_p=s.min_p, mass=list(s.mass)[: self.nv],
                     branch=dict(zip(("ao", "r5", "r7", "r9"), list(s.branch))))
 
+    def autotune(self):
+        """Pick each stage kernel's block size by timing it on the current state."""
+        t = (ctypes.c_int * 6)()
+        _check(lib().cgks_autotune(self.h, t), "cgks_autotune")
+        return dict(zip(("lines", "normal", "flux1", "flux2", "update1", "update2"), list(t)))
+
     def kernels_per_step(self):
         n = ctypes.c_int()
         _check(lib().cgks_step_info(self.h, ctypes.byref(n)), "cgks_step_info")
@@ -276,6 +285,11 @@ class Batch:
 
     def sync(self):
         _check(lib().cgks_batch_sync(self.h), "cgks_batch_sync")
+
+    def autotune(self):
+        t = (ctypes.c_int * 6)()
+        _check(lib().cgks_batch_autotune(self.h, t), "cgks_batch_autotune")
+        return dict(zip(("lines", "normal", "flux1", "flux2", "update1", "update2"), list(t)))
 
     def get_state(self, k):
         c = (4, self.ny[k], self.nx[k])

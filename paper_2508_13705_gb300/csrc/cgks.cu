@@ -87,6 +87,7 @@ struct cgks_batch {
     char* slab = nullptr;
     Kfns k;
     int grid[16];
+    int threads[16];  // threads per block of each kernel slot (autotuned)
     int nsm = 0;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // [0] fixed dt, [1] CFL dt
     int kernels_per_step = 0;
@@ -131,7 +132,7 @@ int launch(cgks_batch* b, const void* fn, int kind, int gi, int stage, bool has_
 {
     Work w = work_of(b, kind);
     if (w.total == 0) return CGKS_OK;
-    int threads = (kind == W_FLUX) ? 128 : 256;
+    int threads = b->threads[gi];
     long long need = (w.total + threads - 1) / threads;
     int grid = (int)std::min<long long>(need, (long long)b->grid[gi]);
     if (grid < 1) grid = 1;
@@ -355,8 +356,9 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
                               (const void*)b->k.cfl};
         for (int q = 0; q < 7; ++q) {
             int occ = 1;
+            int th = (q == 2 || q == 3) ? 128 : 256;
+            b->threads[q] = th;
             if (fns[q]) {
-                int th = (q == 2 || q == 3) ? 128 : 256;
                 if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fns[q], th, 0) != cudaSuccess) occ = 1;
             }
             b->grid[q] = std::max(1, occ) * b->nsm;
@@ -468,7 +470,103 @@ int post_set(cgks_batch* b, bool init_sigma)
 
 } // namespace
 
+namespace {
+
+// Persistent grid for a kernel at a given block size: SM count x resident blocks.
+int grid_for(cgks_batch* b, const void* fn, int threads)
+{
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, 0) != cudaSuccess || occ < 1) occ = 1;
+    return occ * b->nsm;
+}
+
+// Time each stage kernel at every admissible block size on the current state
+// and keep the fastest.  Only kernels that write scratch data run (stage 1
+// lines / normal / flux / update and the stage-2 flux); the simulated time is
+// restored afterwards.  The step graphs are rebuilt on next use.
+int autotune(cgks_batch* b, int* out)
+{
+    if (!b->state_set) return CGKS_EINVAL;
+    // tuning order: each kernel runs after the producers of its inputs (the
+    // stage-2 flux before the stage-1 flux, so the update sees stage-1 data)
+    const void* fns[5] = {(const void*)b->k.lines, (const void*)b->k.normal, (const void*)b->k.flux2,
+                          (const void*)b->k.flux1, (const void*)b->k.upd1};
+    const int slots[5] = {0, 1, 3, 2, 4};
+    const int kinds[5] = {W_LINES, W_NORMAL, W_FLUX, W_FLUX, W_CELLS};
+    const int stages[5] = {1, 1, 0, 0, 0};
+    const bool has_stage[5] = {true, true, false, false, false};
+    std::vector<double> t_saved(b->n);
+    for (int k = 0; k < b->n; ++k) CK(cudaMemcpy(&t_saved[k], b->host[k].t, 8, cudaMemcpyDeviceToHost));
+    // a CFL time step so that every kernel sees the data of a real step
+    int r = launch(b, (const void*)b->k.cfl, W_CELLS, 6, 0, false);
+    if (r) return r;
+    {
+        int use = 1;
+        const double* fx = b->dfixed;
+        Mesh* dm = b->dmesh;
+        int nn = b->n;
+        void* args[] = {&dm, &nn, &use, &fx};
+        CK(cudaLaunchKernel((const void*)k_dt<0>, dim3((nn + 127) / 128), dim3(128), args, 0, b->stream));
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int qq = 0; qq < 5; ++qq) {
+        if (!fns[qq]) continue;
+        int q = slots[qq];
+        cudaFuncAttributes at;
+        CK(cudaFuncGetAttributes(&at, fns[qq]));
+        int best_t = b->threads[q], best_g = b->grid[q];
+        float best = 1e30f;
+        const int cand[4] = {64, 128, 256, 512};
+        for (int c = 0; c < 4; ++c) {
+            int th = cand[c];
+            if (th > at.maxThreadsPerBlock) continue;
+            b->threads[q] = th;
+            b->grid[q] = grid_for(b, fns[qq], th);
+            float acc = 0.f;
+            for (int rep = 0; rep < 4; ++rep) {
+                CK(cudaEventRecord(e0, b->stream));
+                if ((r = launch(b, fns[qq], kinds[qq], q, stages[qq], has_stage[qq]))) return r;
+                CK(cudaEventRecord(e1, b->stream));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0) acc += ms;  // the first launch warms caches
+            }
+            if (acc < best) { best = acc; best_t = th; best_g = b->grid[q]; }
+        }
+        b->threads[q] = best_t;
+        b->grid[q] = best_g;
+    }
+    // stage-2 update shares the stage-1 update's shape
+    b->threads[5] = b->threads[4];
+    b->grid[5] = grid_for(b, (const void*)b->k.upd2, b->threads[5]);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int k = 0; k < b->n; ++k) CK(cudaMemcpy(b->host[k].t, &t_saved[k], 8, cudaMemcpyHostToDevice));
+    for (int g = 0; g < 2; ++g)
+        if (b->gexec[g]) { cudaGraphExecDestroy(b->gexec[g]); b->gexec[g] = nullptr; }
+    if (out)
+        for (int q = 0; q < 6; ++q) out[q] = b->threads[q];
+    return CGKS_OK;
+}
+
+} // namespace
+
 extern "C" {
+
+int cgks_autotune(cgks_solver* s, int* threads_out)
+{
+    if (!s) return CGKS_EINVAL;
+    return autotune(s->b, threads_out);
+}
+
+int cgks_batch_autotune(cgks_batch* b, int* threads_out)
+{
+    if (!b) return CGKS_EINVAL;
+    return autotune(b, threads_out);
+}
 
 int cgks_default_params(cgks_params* p, int dim, int order)
 {

@@ -327,3 +327,31 @@ def test_fp32_bulk_quadrants_per_step():
         s.sync()
         o.step(dt)
         assert rel_l1(s.get_state()["W"], o.W) < 1e-6
+
+
+# ---------------------------------------------------------------- autotuner
+
+def test_autotune_keeps_results_bitwise_and_state():
+    """The autotuner changes only launch shapes: the state is not advanced and
+    the following steps are bitwise equal to an untuned solver's."""
+    n = 40
+    st = inputs.quadrants_2d(n, 9, seed=2)
+    kw = dict(tau_mode=cgks.TAU_HGKS, bc=(1, 1, 1, 1))
+    outs = []
+    for tune in (False, True):
+        s = cgks.Solver(2, 9, n, n, **kw)
+        s.set_state(*st)
+        if tune:
+            before = s.get_state()
+            choice = s.autotune()
+            assert set(choice) >= {"lines", "normal", "flux1", "update1"}
+            assert all(c in (64, 128, 256, 512) for c in choice.values())
+            after = s.get_state()
+            for f in FIELDS_2D:
+                assert np.array_equal(before[f], after[f]), f
+        s.advance(4, 0.0)
+        t, rc, _ = s.sync()
+        outs.append((t, s.get_state()))
+    assert outs[0][0] == outs[1][0]
+    for f in FIELDS_2D:
+        assert np.array_equal(outs[0][1][f], outs[1][1][f]), f
