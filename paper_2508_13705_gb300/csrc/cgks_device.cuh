@@ -246,43 +246,47 @@ __device__ __forceinline__ Dff dff_select(int order, const double s[6], double t
     return d;
 }
 
-// Packed form of a Dff for a per-cell buffer: (a0, a1, a3, stencil code)
+// A cell's DFF choice in the bulk precision R: the DFFs of S0, S1, S2 = r5
+// (a[2] == a[3]) and the stencil code (-1 HWENO-AO, else r5/r7/r9).  On the
+// linear branches the chosen stencil's DFF is 1 (Algorithm 1 only takes a
+// linear stencil whose DFF is 1), so only the HWENO-AO branch scales.
 template <typename R>
-__device__ __forceinline__ void dff_pack(const Dff& d, R out[4])
+struct DffR {
+    R a[4];
+    int st;
+};
+
+template <typename R>
+__device__ __forceinline__ DffR<R> dff_r(const Dff& d)
 {
-    out[0] = (R)d.a[0]; out[1] = (R)d.a[1]; out[2] = (R)d.a[3]; out[3] = (R)d.st;
+    DffR<R> r;
+    for (int k = 0; k < 4; ++k) r.a[k] = (R)d.a[k];
+    r.st = d.st;
+    return r;
+}
+
+// Packed form for a per-cell buffer: (a0, a1, a3, stencil code)
+template <typename R>
+__device__ __forceinline__ void dff_pack(const DffR<R>& d, R out[4])
+{
+    out[0] = d.a[0]; out[1] = d.a[1]; out[2] = d.a[3]; out[3] = (R)d.st;
 }
 template <typename R>
-__device__ __forceinline__ Dff dff_unpack(const R in[4])
+__device__ __forceinline__ DffR<R> dff_unpack(const R in[4])
 {
-    Dff d;
-    d.a[0] = (double)in[0]; d.a[1] = (double)in[1]; d.a[2] = d.a[3] = (double)in[2];
+    DffR<R> d;
+    d.a[0] = in[0]; d.a[1] = in[1]; d.a[2] = d.a[3] = in[2];
     d.st = (int)in[3];
-    d.alpha = d.st < 0 ? d.a[3] : 1.0;
     return d;
 }
 
-// Evaluate NOUT functionals (rows ROW0.., value rows flagged by the mask)
-// of the ASE-DFF polynomial of one cell.  dp[10]: data relative to the own
-// cell: [Qbar_{i+k} - Qbar_i (k=-2..2), h*Qx_{i+k}]; qi = Qbar_i.
-// Value outputs are returned relative to qi as well.
+// HWENO-AO(5,3) with DFF-scaled sub-polynomials (Eq. 3.11-3.17, 3.19) for
+// NOUT consecutive functional rows starting at row0.  Kept out of line: the
+// branch is rare, and inlining it in every variable's loop bloats the kernels.
 template <typename R, int NOUT>
-__device__ __forceinline__ void recon(const Dff& dff, int oi, const int* rows, unsigned value_mask,
-                                      const R dp[10], R out[NOUT], double ghi, double glo, double eps)
+__device__ __noinline__ void recon_ao(const R* al, int oi, int row0, const R* dp, R* out, R ghi, R glo, R eps)
 {
     const auto& T = Tab<R>::get(oi);
-    if (dff.st >= 0) {
-        R al = (R)dff.alpha;
-#pragma unroll
-        for (int r = 0; r < NOUT; ++r) {
-            R s = 0;
-#pragma unroll
-            for (int k = 0; k < 10; ++k) s += T.row[dff.st][rows[r]][k] * dp[k];
-            out[r] = al * s;  // Eq. 3.5: Q_i + alpha (p - Q_i), derivatives alpha p'
-        }
-        return;
-    }
-    // HWENO-AO(5,3) with DFF-scaled sub-polynomials (Eq. 3.11-3.17, 3.19)
     R beta[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -306,16 +310,15 @@ __device__ __forceinline__ void recon(const Dff& dff, int oi, const int* rows, u
 #pragma unroll
                 for (int y = 1; y < 5; ++y) b += c[x] * c[y] * T.bm4[x][y];
         }
-        R ak = (R)dff.a[k];
-        beta[k] = ak * ak * b;  // smoothness of the DFF-scaled polynomial
+        beta[k] = al[k] * al[k] * b;  // smoothness of the DFF-scaled polynomial
     }
-    R g3 = (R)ghi, g2 = (R)((1.0 - ghi) * glo), g0 = (R)((1.0 - ghi) * (1.0 - glo) * 0.5);
+    R g3 = ghi, g2 = ((R)1 - ghi) * glo, g0 = ((R)1 - ghi) * ((R)1 - glo) * (R)0.5;
     R gk[4] = {g0, g0, g2, g3};
     R tz = (fabs(beta[3] - beta[0]) + fabs(beta[3] - beta[1]) + fabs(beta[3] - beta[2])) / (R)3;
     R w[4], ws = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        R q = tz / (beta[k] + (R)eps);
+        R q = tz / (beta[k] + eps);
         w[k] = gk[k] * ((R)1 + q * q);
         ws += w[k];
     }
@@ -331,12 +334,33 @@ __device__ __forceinline__ void recon(const Dff& dff, int oi, const int* rows, u
         for (int k = 0; k < 4; ++k) {
             R p = 0;
 #pragma unroll
-            for (int q = 0; q < 10; ++q) p += T.row[k][rows[r]][q] * dp[q];
-            s += (k == 3 ? c3 : ck[k]) * (R)dff.a[k] * p;
+            for (int q = 0; q < 10; ++q) p += T.row[k][row0 + r][q] * dp[q];
+            s += (k == 3 ? c3 : ck[k]) * al[k] * p;
         }
         out[r] = s;
     }
-    (void)value_mask;
+}
+
+// Evaluate NOUT consecutive functional rows (from row0) of the ASE-DFF
+// polynomial of one cell.  dp[10]: data relative to the own cell:
+// [Qbar_{i+k} - Qbar_i (k=-2..2), h*Qx_{i+k}]; values come out relative to
+// Qbar_i too (Eq. 3.5: Q_i + alpha (p - Q_i), derivatives alpha p').
+template <typename R, int NOUT>
+__device__ __forceinline__ void recon(const DffR<R>& dff, int oi, int row0, const R dp[10], R out[NOUT],
+                                      R ghi, R glo, R eps)
+{
+    if (dff.st >= 0) {
+        const auto& T = Tab<R>::get(oi);
+#pragma unroll
+        for (int r = 0; r < NOUT; ++r) {
+            R s = 0;
+#pragma unroll
+            for (int k = 0; k < 10; ++k) s += T.row[dff.st][row0 + r][k] * dp[k];
+            out[r] = s;
+        }
+        return;
+    }
+    recon_ao<R, NOUT>(dff.a, oi, row0, dp, out, ghi, glo, eps);
 }
 
 // ------------------------------------------------------------------ kinetics

@@ -101,11 +101,8 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         double s6[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) s6[q] = lsigT(g, g.sig_x, g.sig_y, dir, a, b - 2 + q);
-        Dff dff = dff_select(g.order, s6, g.thr);
+        DffR<R> dff = dff_r<R>(dff_select(g.order, s6, g.thr));
         R ht = (R)(dir == 0 ? g.dy : g.dx);
-        int rows[M];
-#pragma unroll
-        for (int l = 0; l < M; ++l) rows[l] = 6 + l;
         long long cidx = cell_idx(dir, na, nb, a, b);
         R* LA = (R*)g.LA[dir] + cidx * M * 4;
         // tangential r5 DFF of this cell, reused by Step 3 in k_flux
@@ -116,7 +113,7 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
 #pragma unroll
             for (int q = 0; q < 6; ++q) n6[q] = lsigN<2>(g, g.sig_x, g.sig_y, dir, a - 2 + q, b);
             R pk[4];
-            dff_pack<R>(dff_select(g.order, n6, g.thr), pk);
+            dff_pack<R>(dff_r<R>(dff_select(g.order, n6, g.thr)), pk);
             st4((R*)g.DN[dir] + cidx * 4, pk);
         }
         // the tangential stencil: a direct walk for interior cells
@@ -148,7 +145,7 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
                 }
             }
             R out[M];
-            recon<R, M>(dff, g.oi, rows, 0, dp, out, g.ghi, g.glo, g.eps);
+            recon<R, M>(dff, g.oi, 6, dp, out, (R)g.ghi, (R)g.glo, (R)g.eps);
 #pragma unroll
             for (int l = 0; l < M; ++l) res[l][v] = qi + out[l];
         }
@@ -186,7 +183,7 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
         long long cidx = cell_idx(dir, na, nb, a, b);
         long long lstr = dir == 0 ? 1 : (nb + 2);  // LA stride between normal neighbours
-        Dff dff;
+        DffR<R> dff;
         if (D == 2) {
             R pk[4];
             ld4((const R*)g.DN[dir] + cidx * 4, pk);
@@ -195,14 +192,16 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
             double s6[6];
 #pragma unroll
             for (int q = 0; q < 6; ++q) s6[q] = sigx<1>(g, g.sig_x, a - 2 + q, 0);
-            dff = dff_select(g.order, s6, g.thr);
+            dff = dff_r<R>(dff_select(g.order, s6, g.thr));
         }
         {
+            // branch counts, aggregated per warp
             int bi = dff.st < 0 ? 0 : dff.st - ST_R5 + 1;
-            atomicAdd(&cnt[bi], 1ull);
+            unsigned act = __activemask();
+            unsigned same = __match_any_sync(act, bi);
+            if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&cnt[bi], (unsigned long long)__popc(same));
         }
         R hn = (R)(dir == 0 ? g.dx : g.dy);
-        const int rows[6] = {0, 1, 2, 3, 4, 5};
         R* FR = (R*)g.FR[dir];
         // the line averages of the five stencil cells on this Gauss line
         R la5[5][4];
@@ -243,7 +242,7 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
                 }
             }
             R out[6];
-            recon<R, 6>(dff, g.oi, rows, 0, dp, out, g.ghi, g.glo, g.eps);
+            recon<R, 6>(dff, g.oi, 0, dp, out, (R)g.ghi, (R)g.glo, (R)g.eps);
             R ih = (R)1 / hn;
             sideL[0][v] = qi + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
             sideR[0][v] = qi + out[3]; sideR[1][v] = out[4] * ih; sideR[2][v] = out[5] * ih * ih;
@@ -399,7 +398,6 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
         const Mesh& g = w.mesh[k];
         long long c = gi - w.off[k];
         int i = (int)(c % g.nx), j = (int)(c / g.nx);
-        const auto& T = Tab<double>::get(g.oi);
         const R* FX = (const R*)g.FO[0];
         const R* FY = (const R*)g.FO[1];
         // x-faces: b = j, f = i and i+1; y-faces: b = i, f = j and j+1
@@ -408,14 +406,18 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
         const R* yl = FY + (((long long)j * g.nx + i) * M) * 16;
         const R* yr = yl + (long long)g.nx * M * 16;
         double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
+        const R ridx = (R)idx, ridy = (R)idy;
         long long P = g.plane;
         double* out = STAGE == 1 ? g.S1 : g.S0;
         float* outf = STAGE == 1 ? g.F1 : g.F0;
-        double fx0[4] = {0, 0, 0, 0}, fy0[4] = {0, 0, 0, 0}, fx1[4] = {0, 0, 0, 0}, fy1[4] = {0, 0, 0, 0};
-        double sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
+        const auto& TR = Tab<R>::get(g.oi);
+        // face differences and Gauss sums in the bulk precision (the face data
+        // are bulk values); the cell averages accumulate in FP64 below
+        R fx0[4] = {0, 0, 0, 0}, fy0[4] = {0, 0, 0, 0}, fx1[4] = {0, 0, 0, 0}, fy1[4] = {0, 0, 0, 0};
+        R sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
 #pragma unroll 1
         for (int l = 0; l < M; ++l) {
-            double wl = T.gw[l];
+            R wl = TR.gw[l];
             R a[4], bq[4], cq[4], dq[4];
             // stage 1: o0 = F(dt/2), o1 = dt F + dt^2/6 F_t, o2 = W(dt/2), o3 = W0 + dt W_t + dt^2/6 W_tt
             // stage 2: o0 = dt^2/3 F_t*, o1 = dt^2/3 W_tt*
@@ -427,8 +429,8 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
                 ld4(yl + l * 16 + q * 4, dq);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                    double dx_ = (double)a[v] - (double)bq[v];
-                    double dy_ = (double)cq[v] - (double)dq[v];
+                    R dx_ = a[v] - bq[v];
+                    R dy_ = cq[v] - dq[v];
                     if (q == 0) {
                         fx0[v] += wl * dx_;
                         fy0[v] += wl * dy_;
@@ -436,23 +438,23 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
                         fx1[v] += wl * dx_;
                         fy1[v] += wl * dy_;
                     } else if ((STAGE == 1 && q == 2) || (STAGE == 2 && q == 1)) {
-                        double lx = dx_ * idx, ly = dy_ * idy;
+                        R lx = dx_ * ridx, ly = dy_ * ridy;
                         if (STAGE == 2) {
-                            lx += g.ACC[(4 + 4 * l + v) * P + c];
-                            ly += g.ACC[(4 + 4 * M + 4 * l + v) * P + c];
+                            lx += (R)g.ACC[(4 + 4 * l + v) * P + c];
+                            ly += (R)g.ACC[(4 + 4 * M + 4 * l + v) * P + c];
                         }
                         if (BULK32) {
                             outf[(12 + 4 * l + v) * P + c] = (float)lx;
                             outf[(12 + 4 * M + 4 * l + v) * P + c] = (float)ly;
                         } else {
-                            out[(12 + 4 * l + v) * P + c] = lx;
-                            out[(12 + 4 * M + 4 * l + v) * P + c] = ly;
+                            out[(12 + 4 * l + v) * P + c] = (double)lx;
+                            out[(12 + 4 * M + 4 * l + v) * P + c] = (double)ly;
                         }
                         sx[v] += wl * lx;
                         sy[v] += wl * ly;
                     } else {  // stage 1, q == 3: line-slope part of the accumulator
-                        g.ACC[(4 + 4 * l + v) * P + c] = dx_ * idx;
-                        g.ACC[(4 + 4 * M + 4 * l + v) * P + c] = dy_ * idy;
+                        g.ACC[(4 + 4 * l + v) * P + c] = (double)(dx_ * ridx);
+                        g.ACC[(4 + 4 * M + 4 * l + v) * P + c] = (double)(dy_ * ridy);
                     }
                 }
             }
@@ -463,10 +465,10 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
             double Wn;
             if (STAGE == 1) {
                 double W = g.S0[v * P + c];
-                Wn = W - fx0[v] * idx - fy0[v] * idy;               // Eq. 2.21
-                g.ACC[v * P + c] = W - fx1[v] * idx - fy1[v] * idy;
+                Wn = W - (double)fx0[v] * idx - (double)fy0[v] * idy;               // Eq. 2.21
+                g.ACC[v * P + c] = W - (double)fx1[v] * idx - (double)fy1[v] * idy;
             } else {
-                Wn = g.ACC[v * P + c] - fx0[v] * idx - fy0[v] * idy;  // Eq. 2.22-2.23
+                Wn = g.ACC[v * P + c] - (double)fx0[v] * idx - (double)fy0[v] * idy;  // Eq. 2.22-2.23
             }
             out[v * P + c] = Wn;
             bad |= !isfinite(Wn);
@@ -475,8 +477,8 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
                 outf[(4 + v) * P + c] = (float)sx[v];  // cell slopes: Gauss sum of the line slopes
                 outf[(8 + v) * P + c] = (float)sy[v];
             } else {
-                out[(4 + v) * P + c] = sx[v];
-                out[(8 + v) * P + c] = sy[v];
+                out[(4 + v) * P + c] = (double)sx[v];
+                out[(8 + v) * P + c] = (double)sy[v];
             }
         }
         // face sigma of this step (Eq. 3.1): mean over the face's Gauss points
