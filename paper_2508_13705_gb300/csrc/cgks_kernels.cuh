@@ -269,10 +269,16 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
 }
 
 // -------------------------------------------------------------- Step 3 + flux
+// One thread per face Gauss point.  The two sides stream through one at a
+// time: each side's reconstructed data (Step 2 values, Step 3 tangential
+// derivatives), its Maxwellian half-range moments and micro-slopes are folded
+// into the kinetic weighting Q0, dQ0 (Eq. 2.7) and the half-range terms of
+// Eq. 2.6 as soon as they are formed, so only one side is live at a time.
 template <int D, int M, typename R, int STAGE>
 __global__ void __launch_bounds__(128) k_flux(Work w)
 {
     constexpr int NV = D + 2;
+    constexpr int ND = D == 2 ? 5 : 2;  // derivatives: n, nn (, t, tt, nt)
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
          gi += (long long)gridDim.x * blockDim.x) {
         int k = find_mesh(w, gi);
@@ -291,12 +297,25 @@ __global__ void __launch_bounds__(128) k_flux(Work w)
         if (dir == 0) { f = (int)(r % (na + 1)); b = D == 2 ? (int)(r / (na + 1)) : 0; }
         else { b = (int)(r % nb); f = (int)(r / nb); }
         const R* FR = (const R*)g.FR[dir];
-        SideData<R, D> sd[2];
+        const R gm = (R)g.gamma, K = (R)g.K;
+        const bool hgks = g.tau_mode == 1;
+        R e1[4] = {1, 0, 0, 0};
+        R Q0[4] = {0, 0, 0, 0};
+        R dQ[ND][4];
 #pragma unroll
+        for (int q = 0; q < ND; ++q)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) dQ[q][v] = 0;
+        R T5[4] = {0, 0, 0, 0}, T6[4] = {0, 0, 0, 0}, S1h[4] = {0, 0, 0, 0};
+        R pz[2], mn[2], mt[2];
+        bool bad = false, ok = true;
+#pragma unroll 1
         for (int side = 0; side < 2; ++side) {
+            // Step 2 data: W, W_n, W_nn
+            R d[6][4];
             const R* fr = FR + ((fr_row(dir, na, nb, b + 1, f) * M + l) * 2 + side) * 12;
 #pragma unroll
-            for (int nd = 0; nd < 3; ++nd) ld4(fr + nd * 4, sd[side].d[nd]);
+            for (int nd = 0; nd < 3; ++nd) ld4(fr + nd * 4, d[nd]);
             if (D == 2) {
                 // Step 3: tangential derivatives from the 3M face points of
                 // segments b-1, b, b+1, scaled by the tangential r5 DFF of the
@@ -325,37 +344,160 @@ __global__ void __launch_bounds__(128) k_flux(Work w)
                     }
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                    sd[side].d[3][v] = c1 * wt[v];
-                    sd[side].d[4][v] = c2 * wtt[v];
-                    sd[side].d[5][v] = c1 * wnt[v];
+                    d[3][v] = c1 * wt[v];
+                    d[4][v] = c2 * wtt[v];
+                    d[5][v] = c1 * wnt[v];
+                }
+            }
+            // Eq. 3.2 ingredients and the positivity test, in the precision the
+            // states carry (the face means, stencil sums and branch thresholds
+            // that use sigma are FP64)
+            {
+                R rho = d[0][0];
+                R ir = (R)1 / rho;
+                R un = d[0][1] * ir;
+                R ut = D == 2 ? d[0][2] * ir : (R)0;
+                R p = (gm - (R)1) * (d[0][NV - 1] - (R)0.5 * rho * (un * un + ut * ut));
+                R ic = (R)1 / sqrt(gm * p * ir);
+                pz[side] = p; mn[side] = un * ic; mt[side] = ut * ic;
+                bad |= !(rho > (R)0) || !(p > (R)0);
+            }
+            // kinetic weighting (Eq. 2.7): this side's half-range integrals
+            Mom<R, D> Ms;
+            ok &= maxwellian<R, D>(d[0], gm, K, side == 0 ? 1 : 2, Ms);
+            R t[4], z[4];
+            mom<R, D>(Ms, e1, 0, 0, t);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) Q0[v] += Ms.rho * t[v];
+            if (hgks) {
+                mom<R, D>(Ms, e1, 1, 0, t);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) T5[v] += Ms.rho * t[v];
+            }
+#pragma unroll
+            for (int q = 0; q < ND; ++q) {
+                R a[4];
+                slope<R, D>(Ms, K, d[q + 1], a);  // <a> = dW of this side (Eq. 2.8)
+                mom<R, D>(Ms, a, 0, 0, t);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) dQ[q][v] += Ms.rho * t[v];
+                if (hgks && (q == 0 || (D == 2 && q == 2))) {
+                    // half-range (a_n u + a_t v) terms of Eq. 2.6, with and without the flux's u
+                    int pu = q == 0 ? 1 : 0, pv = q == 0 ? 0 : 1;
+                    mom<R, D>(Ms, a, pu, pv, t);
+                    mom<R, D>(Ms, a, pu + 1, pv, z);
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) { S1h[v] += Ms.rho * t[v]; T6[v] += Ms.rho * z[v]; }
                 }
             }
         }
-        // Eq. 3.2 sigma and the positivity test of the reconstructed states,
-        // evaluated in the precision the states carry (the face means, stencil
-        // sums and branch thresholds that use sigma are FP64)
-        R pz[2], mn[2], mt[2];
-        bool bad = false;
-        const R gm = (R)g.gamma;
-#pragma unroll
-        for (int side = 0; side < 2; ++side) {
-            R rho = sd[side].d[0][0];
-            R ir = (R)1 / rho;
-            R un = sd[side].d[0][1] * ir;
-            R ut = D == 2 ? sd[side].d[0][2] * ir : (R)0;
-            R p = (gm - (R)1) * (sd[side].d[0][NV - 1] - (R)0.5 * rho * (un * un + ut * ut));
-            R ic = (R)1 / sqrt(gm * p * ir);
-            pz[side] = p; mn[side] = un * ic; mt[side] = ut * ic;
-            bad |= !(rho > (R)0) || !(p > (R)0);
+        double sig;
+        {
+            R dpz = fabs(pz[0] - pz[1]);
+            sig = (double)(dpz / pz[0] + dpz / pz[1] + (mn[0] - mn[1]) * (mn[0] - mn[1]) + (mt[0] - mt[1]) * (mt[0] - mt[1]));
         }
-        R dpz = fabs(pz[0] - pz[1]);
-        double sig = (double)(dpz / pz[0] + dpz / pz[1] + (mn[0] - mn[1]) * (mn[0] - mn[1]) + (mt[0] - mt[1]) * (mt[0] - mt[1]));
+        // equilibrium state g0 and its micro-slopes, time derivatives (Eq. 2.8)
         double dt = *g.dt;
-        R F[4], Ft[4], Q0[4], Wt[4], Wtt[4];
-        bool ok = kinetic<R, D>(sd[0], sd[1], (R)g.gamma, (R)g.K, g.tau_mode, (R)g.c1, (R)g.c2, (R)dt, F, Ft, Q0, Wt, Wtt);
+        const R Dt = (R)dt;
+        Mom<R, D> M0;
+        ok &= maxwellian<R, D>(Q0, gm, K, 0, M0);
+        R S1[4], S2[4], z[4], rhs[4], Ab[4], A1t[4], A2t[4] = {0, 0, 0, 0};
+        R an[4], at2[4];
+        slope<R, D>(M0, K, dQ[0], an);
+        mom<R, D>(M0, an, 1, 0, S1);
+        if (D == 2) {
+            slope<R, D>(M0, K, dQ[2], at2);
+            mom<R, D>(M0, at2, 0, 1, z);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) S1[v] += z[v];
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { S1[v] *= M0.rho; rhs[v] = -S1[v]; }
+        slope<R, D>(M0, K, rhs, Ab);
+        {
+            R ann[4];
+            slope<R, D>(M0, K, dQ[1], ann);
+            mom<R, D>(M0, ann, 1, 0, rhs);
+        }
+        if (D == 2) {
+            R ant[4];
+            slope<R, D>(M0, K, dQ[4], ant);
+            mom<R, D>(M0, ant, 0, 1, z);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) rhs[v] += z[v];
+            R s2[4];
+            mom<R, D>(M0, ant, 1, 0, s2);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) rhs[v] *= -M0.rho;
+            slope<R, D>(M0, K, rhs, A1t);
+            R att[4];
+            slope<R, D>(M0, K, dQ[3], att);
+            mom<R, D>(M0, att, 0, 1, z);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) rhs[v] = -M0.rho * (s2[v] + z[v]);
+            slope<R, D>(M0, K, rhs, A2t);
+        } else {
+#pragma unroll
+            for (int v = 0; v < NV; ++v) rhs[v] *= -M0.rho;
+            slope<R, D>(M0, K, rhs, A1t);
+        }
+        mom<R, D>(M0, A1t, 1, 0, S2);
+        if (D == 2) {
+            mom<R, D>(M0, A2t, 0, 1, z);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) S2[v] += z[v];
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) S2[v] *= M0.rho;
+        // flux terms <u> and <A u>; the linear / quadratic fits of Eq. 2.19-2.20
+        // and 2.29 reduce to F = <u>, F_t = <A u>, W_t = -S1, W_tt = -S2 at tau = 0
+        R F[4], Ft[4], Wt[4], Wtt[4];
+        mom<R, D>(M0, e1, 1, 0, F);
+        mom<R, D>(M0, Ab, 1, 0, Ft);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            F[v] *= M0.rho;
+            Ft[v] *= M0.rho;
+            Wt[v] = -S1[v];
+            Wtt[v] = -S2[v];
+        }
+        if (hgks) {
+            R tau = (R)g.c1 * Dt + (R)g.c2 * fabs(pz[0] - pz[1]) / (pz[0] + pz[1]) * Dt;
+            // collision and non-equilibrium terms of Eq. 2.6, fitted analytically
+            R Att[4], T2[4], T3[4], T4[4];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) rhs[v] = -S2[v];
+            slope<R, D>(M0, K, rhs, Att);
+            mom<R, D>(M0, Att, 1, 0, T2);
+            mom<R, D>(M0, an, 2, 0, T3);
+            mom<R, D>(M0, A1t, 2, 0, T4);
+            if (D == 2) {
+                mom<R, D>(M0, at2, 1, 1, z);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) T3[v] += z[v];
+                mom<R, D>(M0, A2t, 1, 1, z);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) T4[v] += z[v];
+            }
+            R ed = exp(-Dt / tau), eh = exp((R)-0.5 * Dt / tau);
+            R h = (R)0.5 * Dt;
+            R E0d = tau * ((R)1 - ed), E0h = tau * ((R)1 - eh);
+            R E1d = tau * tau * ((R)1 - ed) - tau * Dt * ed, E1h = tau * tau * ((R)1 - eh) - tau * h * eh;
+            R f0 = ((R)4 * E0h - E0d) / Dt, g0 = (R)4 * (E0d - (R)2 * E0h) / (Dt * Dt);
+            R f1 = ((R)4 * E1h - E1d) / Dt, g1 = (R)4 * (E1d - (R)2 * E1h) / (Dt * Dt);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                R T3s = T3[v] * M0.rho, T4s = T4[v] * M0.rho, T2s = T2[v] * M0.rho;
+                R T0v = F[v], T1v = Ft[v];
+                F[v] = T0v * ((R)1 - f0) - tau * T1v + (f1 - tau) * T3s + f0 * T5[v] - f1 * T6[v];
+                Ft[v] = -g0 * T0v + T1v - tau * T2s + g1 * T3s - tau * T4s + g0 * T5[v] - g1 * T6[v];
+                R dS = S1[v] - S1h[v];
+                Wt[v] += ((R)2 * eh - ed) * dS;
+                Wtt[v] += (R)4 * (ed - eh) / Dt * dS;
+            }
+        }
         long long pt = pt_idx(dir, na, nb, b, f) * M + l;
         R* FO = (R*)g.FO[dir] + pt * 16;
-        R Dt = (R)dt;
         R o[4][4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
