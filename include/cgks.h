@@ -156,9 +156,11 @@ int cgks_get_stats(cgks_solver* s, cgks_stats* st);
  * resident blocks) and keeps the fastest; the step graph is rebuilt on the
  * next step.  The state is not advanced (only scratch is written; the
  * simulated time is restored) and results do not depend on the choice: every
- * work item is computed by one thread.  threads_out (may be NULL) receives
- * the block sizes of lines, normal, flux (stage 1, 2), update (stage 1, 2).
- * Requires a state (CGKS_EINVAL otherwise). */
+ * work item is computed by one thread.  The flux kernels are also timed in
+ * a register-capped variant (more resident warps, some spilling).
+ * threads_out (may be NULL) receives the block sizes of lines, normal, flux
+ * (stage 1, 2), update (stage 1, 2); a negative flux entry marks the capped
+ * variant.  Requires a state (CGKS_EINVAL otherwise). */
 int cgks_autotune(cgks_solver* s, int* threads_out);
 int cgks_batch_autotune(cgks_batch* b, int* threads_out);
 

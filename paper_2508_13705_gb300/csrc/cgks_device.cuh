@@ -365,10 +365,13 @@ __device__ __forceinline__ void recon(const DffR<R>& dff, int oi, int row0, cons
 
 // ------------------------------------------------------------------ kinetics
 
-// Maxwellian moments per unit density for one velocity range.
+// Maxwellian moments per unit density for one velocity range, with the
+// per-state factors the micro-slope solves reuse (1/rho, 1/(2 lambda),
+// 4 lambda^2 / (K + D), U^2 + V^2 + (K + D) / (2 lambda)).
 template <typename R, int D>
 struct Mom {
     R rho, U, V, lam;
+    R ir, il, c4, cs;
     R mu[7];
     R mv[6];
     R x2, x4;
@@ -379,17 +382,21 @@ template <typename R, int D>
 __device__ __forceinline__ bool maxwellian(const R* W, R gamma, R K, int range, Mom<R, D>& M)
 {
     R rho = W[0];
-    R U = W[1] / rho;
-    R V = D == 2 ? W[2] / rho : (R)0;
+    R ir = (R)1 / rho;
+    R U = W[1] * ir;
+    R V = D == 2 ? W[2] * ir : (R)0;
     R p = (gamma - (R)1) * (W[D + 1] - (R)0.5 * rho * (U * U + V * V));
-    R lam = rho / ((R)2 * p);
+    R lam = (R)0.5 * rho / p;
+    R i2l = p * ir;  // 1 / (2 lambda)
     M.rho = rho; M.U = U; M.V = V; M.lam = lam;
-    R i2l = (R)0.5 / lam;
+    M.ir = ir; M.il = i2l;
+    M.c4 = (R)4 * lam * lam / (K + (R)D);
+    M.cs = U * U + V * V + (K + (R)D) * i2l;
     if (range == 0) {
         M.mu[0] = 1; M.mu[1] = U;
     } else {
         R sl = sqrt(lam);
-        R e = exp(-lam * U * U) * (R)0.28209479177387814 / sl;  // 1/(2 sqrt(pi lam))
+        R e = exp(-lam * U * U) * (R)0.28209479177387814 * rsqrt(lam);  // e^{-lam U^2} / (2 sqrt(pi lam))
         if (range == 1) { M.mu[0] = (R)0.5 * erfc(-sl * U); M.mu[1] = U * M.mu[0] + e; }
         else { M.mu[0] = (R)0.5 * erfc(sl * U); M.mu[1] = U * M.mu[0] - e; }
     }
@@ -433,30 +440,28 @@ __device__ __forceinline__ void mom(const Mom<R, D>& M, const R* a, int p, int q
     }
 }
 
-// Closed-form solution of <a> = b (full-range moments, Eq. 2.8).
+// Closed-form solution of <a> = b (full-range moments, Eq. 2.8), using the
+// per-state factors of the Maxwellian.
 template <typename R, int D>
 __device__ __forceinline__ void slope(const Mom<R, D>& M, R K, const R* b, R* a)
 {
-    R ir = (R)1 / M.rho;
-    R il = (R)0.5 / M.lam;
+    (void)K;
     if (D == 2) {
-        R B0 = b[0] * ir, B1 = b[1] * ir, B2 = b[2] * ir, B3 = b[3] * ir;
-        R c = M.U * M.U + M.V * M.V + (K + (R)2) * il;
+        R B0 = b[0] * M.ir, B1 = b[1] * M.ir, B2 = b[2] * M.ir, B3 = b[3] * M.ir;
         R R2 = B1 - M.U * B0, R3 = B2 - M.V * B0;
-        R R4 = (R)2 * B3 - c * B0;
-        R a4 = (R)4 * M.lam * M.lam / (K + (R)2) * (R4 - (R)2 * M.U * R2 - (R)2 * M.V * R3);
+        R R4 = (R)2 * B3 - M.cs * B0;
+        R a4 = M.c4 * (R4 - (R)2 * M.U * R2 - (R)2 * M.V * R3);
         R a3 = (R)2 * M.lam * R3 - M.V * a4;
         R a2 = (R)2 * M.lam * R2 - M.U * a4;
-        a[0] = B0 - M.U * a2 - M.V * a3 - (R)0.5 * a4 * c;
+        a[0] = B0 - M.U * a2 - M.V * a3 - (R)0.5 * a4 * M.cs;
         a[1] = a2; a[2] = a3; a[3] = a4;
     } else {
-        R B0 = b[0] * ir, B1 = b[1] * ir, B2 = b[2] * ir;
-        R c = M.U * M.U + (K + (R)1) * il;
+        R B0 = b[0] * M.ir, B1 = b[1] * M.ir, B2 = b[2] * M.ir;
         R R2 = B1 - M.U * B0;
-        R R3 = (R)2 * B2 - c * B0;
-        R a3 = (R)4 * M.lam * M.lam / (K + (R)1) * (R3 - (R)2 * M.U * R2);
+        R R3 = (R)2 * B2 - M.cs * B0;
+        R a3 = M.c4 * (R3 - (R)2 * M.U * R2);
         R a2 = (R)2 * M.lam * R2 - M.U * a3;
-        a[0] = B0 - M.U * a2 - (R)0.5 * a3 * c;
+        a[0] = B0 - M.U * a2 - (R)0.5 * a3 * M.cs;
         a[1] = a2; a[2] = a3;
     }
 }

@@ -274,11 +274,25 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
 // derivatives), its Maxwellian half-range moments and micro-slopes are folded
 // into the kinetic weighting Q0, dQ0 (Eq. 2.7) and the half-range terms of
 // Eq. 2.6 as soon as they are formed, so only one side is live at a time.
-template <int D, int M, typename R, int STAGE>
-__global__ void __launch_bounds__(128) k_flux(Work w)
+// CAP = 1 asks for at least 4 resident blocks of 128 threads (<= 128 registers,
+// spilling the rest); CAP = 0 for 3 in FP32 (<= 170 registers, no spills) and
+// 1 in FP64.  The autotuner times both variants.
+template <int D, int M, typename R, int STAGE, int CAP>
+__global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flux(Work w)
 {
     constexpr int NV = D + 2;
     constexpr int ND = D == 2 ? 5 : 2;  // derivatives: n, nn (, t, tt, nt)
+    // Step 3 weights in shared memory: the Gauss line differs across the lanes
+    // of a warp, which would serialise constant-memory reads
+    __shared__ R s_d1[4][12], s_d2[4][12];
+    if (D == 2) {
+        const auto& T = Tab<R>::get(w.mesh[0].oi);  // a table shares one order
+        for (int q = threadIdx.x; q < 48; q += blockDim.x) {
+            s_d1[q / 12][q % 12] = T.d1[q / 12][q % 12];
+            s_d2[q / 12][q % 12] = T.d2[q / 12][q % 12];
+        }
+        __syncthreads();
+    }
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
          gi += (long long)gridDim.x * blockDim.x) {
         int k = find_mesh(w, gi);
@@ -323,7 +337,6 @@ __global__ void __launch_bounds__(128) k_flux(Work w)
                 int a = side == 0 ? f - 1 : f;
                 R at = ((const R*)g.AT[dir])[cell_idx(dir, na, nb, a, b)];
                 R iht = (R)1 / (R)(dir == 0 ? g.dy : g.dx);
-                const auto& T = Tab<R>::get(g.oi);
                 R c1 = at * iht, c2 = at * iht * iht;
                 R wt[4] = {0, 0, 0, 0}, wtt[4] = {0, 0, 0, 0}, wnt[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -334,7 +347,7 @@ __global__ void __launch_bounds__(128) k_flux(Work w)
                         R x0[4], x1[4];
                         ld4(q, x0);
                         ld4(q + 4, x1);
-                        R w1 = T.d1[l][s * M + kk], w2 = T.d2[l][s * M + kk];
+                        R w1 = s_d1[l][s * M + kk], w2 = s_d2[l][s * M + kk];
 #pragma unroll
                         for (int v = 0; v < 4; ++v) {
                             wt[v] += w1 * x0[v];

@@ -19,8 +19,12 @@ Kfns make_kfns()
     Kfns k;
     k.lines = D == 2 ? (KStage)k_lines<M, R> : nullptr;
     k.normal = k_normal<D, M, R>;
-    k.flux1 = k_flux<D, M, R, 1>;
-    k.flux2 = k_flux<D, M, R, 2>;
+    k.flux1v[0] = k_flux<D, M, R, 1, 0>;
+    k.flux2v[0] = k_flux<D, M, R, 2, 0>;
+    k.flux1v[1] = k_flux<D, M, R, 1, 1>;
+    k.flux2v[1] = k_flux<D, M, R, 2, 1>;
+    k.flux1 = k.flux1v[0];
+    k.flux2 = k.flux2v[0];
     if (D == 2) { k.upd1 = (KOne)k_update2<M, R, 1>; k.upd2 = (KOne)k_update2<M, R, 2>; }
     else { k.upd1 = (KOne)k_update1<R, 1>; k.upd2 = (KOne)k_update1<R, 2>; }
     k.cfl = k_cfl<D>;
