@@ -291,6 +291,9 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         g.dy = p->dim == 2 ? (ext[4 * k + 3] - ext[4 * k + 2]) / ny[k] : 1.0;
         g.gamma = p->gamma; g.K = K; g.thr = p->sigma_thres; g.ghi = p->gamma_hi; g.glo = p->gamma_lo;
         g.eps = p->weno_eps; g.c1 = p->tau_c1; g.c2 = p->tau_c2; g.cfl = p->cfl;
+        g.gf = (float)g.gamma; g.Kf = (float)g.K; g.c1f = (float)g.c1; g.c2f = (float)g.c2;
+        g.idx = 1.0 / g.dx; g.idy = 1.0 / g.dy;
+        g.idxf = (float)g.idx; g.idyf = (float)g.idy;
         g.plane = (long long)nx[k] * ny[k];
         char* m0 = b->slab + base[k];
         g.S0 = (double*)(m0 + L[k].S);
@@ -319,6 +322,7 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         g.bad = (long long*)(sc + 24);
         g.smax = (unsigned long long*)(sc + 32);
         g.branch = (unsigned long long*)(sc + 40);
+        g.dtf = (float*)(sc + 72);
         g.ghost = (const double*)(sc + 80);  // 36 doubles of fixed ghost cells (1-D)
     }
     // prefix arrays
@@ -967,6 +971,9 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     g.gamma = p->gamma; g.K = (3.0 - p->gamma) / (p->gamma - 1.0); g.thr = p->sigma_thres;
     g.ghi = p->gamma_hi; g.glo = p->gamma_lo; g.eps = p->weno_eps; g.c1 = p->tau_c1; g.c2 = p->tau_c2;
     g.cfl = p->cfl; g.plane = nx;
+    g.gf = (float)g.gamma; g.Kf = (float)g.K; g.c1f = (float)g.c1; g.c2f = (float)g.c2;
+    g.idx = 1.0 / g.dx; g.idy = 1.0;
+    g.idxf = (float)g.idx; g.idyf = 1.0f;
     g.S0 = state_out;
     g.S1 = (double*)(base + oS1);
     if (rs == 4) {
@@ -980,7 +987,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     unsigned char* sc = base + oSC;
     g.dt = (double*)sc; g.t = (double*)(sc + 8); g.status = (unsigned*)(sc + 16);
     g.bad = (long long*)(sc + 24); g.smax = (unsigned long long*)(sc + 32);
-    g.branch = (unsigned long long*)(sc + 40); g.ghost = (const double*)(sc + 80);
+    g.branch = (unsigned long long*)(sc + 40); g.dtf = (float*)(sc + 72); g.ghost = (const double*)(sc + 80);
     long long off[W_COUNT * 2];
     for (int kind = 0; kind < W_COUNT; ++kind) { off[2 * kind] = 0; off[2 * kind + 1] = items(kind, 1, 1, nx, 1); }
     Mesh* dmesh = (Mesh*)(base + oM);

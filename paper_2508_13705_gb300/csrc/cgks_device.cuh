@@ -63,6 +63,8 @@ struct Mesh {
     int bc[4];
     int tau_mode;
     double dx, dy, gamma, K, thr, ghi, glo, eps, c1, c2, cfl;
+    double idx, idy;                // 1 / dx, 1 / dy
+    float gf, Kf, c1f, c2f, idxf, idyf;  // FP32-bulk copies (no per-point conversions)
     long long plane;                // nx * ny
     // state: planes of nx*ny doubles.  2-D: W[4] Wx[4] Wy[4] Wxl[m][4] Wyl[m][4];
     // 1-D: W[3] Wx[3]
@@ -79,6 +81,7 @@ struct Mesh {
     void* DN[2];                    // normal-direction DFF of each cell, packed [4] (R typed)
     double* SP[2];                  // sigma per face Gauss point
     double* dt;                     // device scalar (this mesh's step)
+    float* dtf;                     // the same in FP32
     double* t;                      // device scalar (simulated time)
     unsigned* status;
     long long* bad;
@@ -107,6 +110,25 @@ __device__ __forceinline__ int find_mesh(const Work& w, long long g)
 __device__ __forceinline__ int imod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
 
 // ------------------------------------------------------------------ ghost cells
+
+// Mesh constants in the bulk precision R.
+template <typename R> struct MeshR;
+template <> struct MeshR<double> {
+    __device__ static double gamma(const Mesh& g) { return g.gamma; }
+    __device__ static double K(const Mesh& g) { return g.K; }
+    __device__ static double c1(const Mesh& g) { return g.c1; }
+    __device__ static double c2(const Mesh& g) { return g.c2; }
+    __device__ static double ih(const Mesh& g, int dir) { return dir == 0 ? g.idx : g.idy; }
+    __device__ static double dt(const Mesh& g) { return *g.dt; }
+};
+template <> struct MeshR<float> {
+    __device__ static float gamma(const Mesh& g) { return g.gf; }
+    __device__ static float K(const Mesh& g) { return g.Kf; }
+    __device__ static float c1(const Mesh& g) { return g.c1f; }
+    __device__ static float c2(const Mesh& g) { return g.c2f; }
+    __device__ static float ih(const Mesh& g, int dir) { return dir == 0 ? g.idxf : g.idyf; }
+    __device__ static float dt(const Mesh& g) { return *g.dtf; }
+};
 
 // The state planes the bulk arithmetic reads: FP64 planes for R = double,
 // the float copies for R = float.  which: 0 state n, 1 stage-1 state.

@@ -98,6 +98,35 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         if (dir == 0) { a = (int)(li % (na + 6)) - 3; b = (int)(li / (na + 6)) - 1; }
         else { b = (int)(li % (nb + 2)) - 1; a = (int)(li / (nb + 2)) - 3; }
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
+        // the tangential stencil: a direct walk for interior cells, whose loads
+        // are issued before the DFF selections so that their latencies overlap
+        bool inner = a >= 0 && a < na && b >= 2 && b + 2 < nb;
+        long long P = g.plane;
+        long long ci = dir == 0 ? (long long)b * g.nx + a : (long long)a * g.nx + b;
+        long long st = dir == 0 ? g.nx : 1;  // tangential neighbour stride
+        int pt = dir == 0 ? 8 : 4;           // plane of the tangential cell slope
+        R sw[4][5], swt[4][5];
+        if (inner) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                int gv = vglob(dir, v);
+                const R* w0 = S + gv * P + ci;
+                const R* wt = S + (pt + gv) * P + ci;
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    sw[v][q] = w0[(q - 2) * st];
+                    swt[v][q] = wt[(q - 2) * st];
+                }
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    sw[v][q] = lcell<2, M, R>(g, S, dir, 0, v, 0, a, b + q - 2);
+                    swt[v][q] = lcell<2, M, R>(g, S, dir, 2, v, 0, a, b + q - 2);
+                }
+        }
         double s6[6];
 #pragma unroll
         for (int q = 0; q < 6; ++q) s6[q] = lsigT(g, g.sig_x, g.sig_y, dir, a, b - 2 + q);
@@ -116,33 +145,14 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
             dff_pack<R>(dff_r<R>(dff_select(g.order, n6, g.thr)), pk);
             st4((R*)g.DN[dir] + cidx * 4, pk);
         }
-        // the tangential stencil: a direct walk for interior cells
-        bool inner = a >= 0 && a < na && b >= 2 && b + 2 < nb;
-        long long P = g.plane;
-        long long ci = dir == 0 ? (long long)b * g.nx + a : (long long)a * g.nx + b;
-        long long st = dir == 0 ? g.nx : 1;  // tangential neighbour stride
-        int pt = dir == 0 ? 8 : 4;           // plane of the tangential cell slope
         R res[M][4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            int gv = vglob(dir, v);
-            R qi, dp[10];
-            if (inner) {
-                const R* w0 = S + gv * P + ci;
-                const R* wt = S + (pt + gv) * P + ci;
-                qi = w0[0];
+            R qi = sw[v][2], dp[10];
 #pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    dp[q] = w0[(q - 2) * st] - qi;
-                    dp[5 + q] = ht * wt[(q - 2) * st];
-                }
-            } else {
-                qi = lcell<2, M, R>(g, S, dir, 0, v, 0, a, b);
-#pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    dp[q] = lcell<2, M, R>(g, S, dir, 0, v, 0, a, b + q - 2) - qi;
-                    dp[5 + q] = ht * lcell<2, M, R>(g, S, dir, 2, v, 0, a, b + q - 2);
-                }
+            for (int q = 0; q < 5; ++q) {
+                dp[q] = sw[v][q] - qi;
+                dp[5 + q] = ht * swt[v][q];
             }
             R out[M];
             recon<R, M>(dff, g.oi, 6, dp, out, (R)g.ghi, (R)g.glo, (R)g.eps);
@@ -217,6 +227,24 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         long long ci = dir == 0 ? (long long)b * g.nx + a : (long long)a * g.nx + b;
         long long sn = dir == 0 ? 1 : g.nx;                    // normal neighbour stride
         int pl0 = (dir == 0 ? 12 : 12 + 4 * M) + 4 * l;         // first line-slope plane of line l
+        // all line slopes of the stencil are loaded before the first
+        // reconstruction, so their latencies overlap
+        R sl[D == 2 ? NV : 1][5];
+        if (D == 2) {
+            if (inner) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    const R* ws = S + (pl0 + vglob(dir, v)) * P + ci;
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) sl[v][q] = ws[(q - 2) * sn];
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) sl[v][q] = lcell<2, M, R>(g, S, dir, 3, v, l, a + q - 2, b);
+            }
+        }
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             R qi;
@@ -225,14 +253,8 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
                 qi = la5[2][v];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) dp[q] = la5[q][v] - qi;
-                if (inner) {
-                    const R* ws = S + (pl0 + vglob(dir, v)) * P + ci;
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) dp[5 + q] = hn * ws[(q - 2) * sn];
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) dp[5 + q] = hn * lcell<2, M, R>(g, S, dir, 3, v, l, a + q - 2, b);
-                }
+                for (int q = 0; q < 5; ++q) dp[5 + q] = hn * sl[D == 2 ? v : 0][q];
             } else {
                 qi = cell<1, 1, R>(g, S, 0, v, 0, a, 0);
 #pragma unroll
@@ -311,7 +333,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         if (dir == 0) { f = (int)(r % (na + 1)); b = D == 2 ? (int)(r / (na + 1)) : 0; }
         else { b = (int)(r % nb); f = (int)(r / nb); }
         const R* FR = (const R*)g.FR[dir];
-        const R gm = (R)g.gamma, K = (R)g.K;
+        const R gm = MeshR<R>::gamma(g), K = MeshR<R>::K(g);
         const bool hgks = g.tau_mode == 1;
         R e1[4] = {1, 0, 0, 0};
         R Q0[4] = {0, 0, 0, 0};
@@ -410,8 +432,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
             sig = (double)(dpz / pz[0] + dpz / pz[1] + (mn[0] - mn[1]) * (mn[0] - mn[1]) + (mt[0] - mt[1]) * (mt[0] - mt[1]));
         }
         // equilibrium state g0 and its micro-slopes, time derivatives (Eq. 2.8)
-        double dt = *g.dt;
-        const R Dt = (R)dt;
+        const R Dt = MeshR<R>::dt(g);
         Mom<R, D> M0;
         ok &= maxwellian<R, D>(Q0, gm, K, 0, M0);
         R S1[4], S2[4], z[4], rhs[4], Ab[4], A1t[4], A2t[4] = {0, 0, 0, 0};
@@ -475,7 +496,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
             Wtt[v] = -S2[v];
         }
         if (hgks) {
-            R tau = (R)g.c1 * Dt + (R)g.c2 * fabs(pz[0] - pz[1]) / (pz[0] + pz[1]) * Dt;
+            R tau = MeshR<R>::c1(g) * Dt + MeshR<R>::c2(g) * fabs(pz[0] - pz[1]) / (pz[0] + pz[1]) * Dt;
             // collision and non-equilibrium terms of Eq. 2.6, fitted analytically
             R Att[4], T2[4], T3[4], T4[4];
 #pragma unroll
@@ -560,10 +581,13 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
         const R* xr = xl + M * 16;
         const R* yl = FY + (((long long)j * g.nx + i) * M) * 16;
         const R* yr = yl + (long long)g.nx * M * 16;
-        double idx = 1.0 / g.dx, idy = 1.0 / g.dy;
-        const R ridx = (R)idx, ridy = (R)idy;
+        const double idx = g.idx, idy = g.idy;
+        const R ridx = MeshR<R>::ih(g, 0), ridy = MeshR<R>::ih(g, 1);
         long long P = g.plane;
         double* out = STAGE == 1 ? g.S1 : g.S0;
+        // line-slope part of the accumulator, held in the bulk precision (a float
+        // view in the FP32-bulk form: it only ever holds bulk values)
+        R* accs = (R*)(g.ACC + 4 * P);
         float* outf = STAGE == 1 ? g.F1 : g.F0;
         const auto& TR = Tab<R>::get(g.oi);
         // face differences and Gauss sums in the bulk precision (the face data
@@ -595,8 +619,8 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
                     } else if ((STAGE == 1 && q == 2) || (STAGE == 2 && q == 1)) {
                         R lx = dx_ * ridx, ly = dy_ * ridy;
                         if (STAGE == 2) {
-                            lx += (R)g.ACC[(4 + 4 * l + v) * P + c];
-                            ly += (R)g.ACC[(4 + 4 * M + 4 * l + v) * P + c];
+                            lx += accs[(4 * l + v) * P + c];
+                            ly += accs[(4 * M + 4 * l + v) * P + c];
                         }
                         if (BULK32) {
                             outf[(12 + 4 * l + v) * P + c] = (float)lx;
@@ -608,8 +632,8 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
                         sx[v] += wl * lx;
                         sy[v] += wl * ly;
                     } else {  // stage 1, q == 3: line-slope part of the accumulator
-                        g.ACC[(4 + 4 * l + v) * P + c] = (double)(dx_ * ridx);
-                        g.ACC[(4 + 4 * M + 4 * l + v) * P + c] = (double)(dy_ * ridy);
+                        accs[(4 * l + v) * P + c] = dx_ * ridx;
+                        accs[(4 * M + 4 * l + v) * P + c] = dy_ * ridy;
                     }
                 }
             }
@@ -679,7 +703,7 @@ __global__ void __launch_bounds__(256) k_update1(Work w)
         const R* FX = (const R*)g.FO[0];
         const R* xl = FX + (long long)i * 16;
         const R* xr = xl + 16;
-        double idx = 1.0 / g.dx;
+        const double idx = g.idx;
         long long P = g.plane;
         bool bad = false;
         for (int v = 0; v < 3; ++v) {
@@ -796,6 +820,7 @@ __global__ void k_dt(Mesh* meshes, int n, int use_cfl, const double* fixed)
             dt = fixed[k];
         }
         *g.dt = dt;
+        *g.dtf = (float)dt;
         *g.t += dt;
         for (int q = 0; q < 4; ++q) g.branch[q] = 0ull;  // counts cover the latest step
     }
