@@ -30,11 +30,24 @@ FP32_PEAK_LANES = 128       # FP32 lanes per SM (Blackwell)
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate (non-tensor), profiling recipe
 HBM_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
-# Algorithmic FP operations per face Gauss point of the flux kernel (stage 1,
-# tau = 0, 2-D, order 9): FADD + FMUL + 2 FFMA (+ DADD/DMUL/2 DFMA) counted by
-# ncu on the flux kernel of a small mesh, divided by the face points of the
-# launch (the kernel evaluates every face point exactly once).
-FLOPS_PER_POINT = {("fp32", 9): 3110.0, ("fp64", 9): 3621.0}
+# Per cell, per launch of each kernel of a stage (2-D, order 9, tau = 0): the
+# FP operations in the bulk precision (FADD + FMUL + 2 FFMA, or the FP64
+# counterparts in the plain form), the FP64 operations of the FP32-bulk form,
+# and the DRAM bytes read + written.  Counted by ncu (one launch each,
+# --clock-control none) on the 1024^2 vortex; every kernel does the same work
+# per cell at any mesh size (one thread per cell line or face point), so a
+# launch on n^2 cells processes n^2 times these.  The flux kernel's operations
+# per face Gauss point are these over 2 m (n + 1) / n points per cell.
+KERNEL_COUNTS = {
+    ("fp32", 9): {"s1_lines": (757.9, 24.1, 213.3), "s1_normal": (4473.4, 0.0, 1159.9),
+                  "s1_flux": (24593.9, 0.0, 1319.5), "s1_update": (384.0, 42.0, 969.7),
+                  "s2_lines": (757.9, 24.1, 214.0), "s2_normal": (4473.4, 0.0, 1164.1),
+                  "s2_flux": (23623.0, 0.0, 1019.8), "s2_update": (256.0, 16.0, 892.1)},
+    ("fp64", 9): {"s1_lines": (782.0, 782.0, 449.6), "s1_normal": (4513.5, 4513.5, 2074.3),
+                  "s1_flux": (26874.3, 26874.3, 2789.1), "s1_update": (426.0, 426.0, 1752.9),
+                  "s2_lines": (782.0, 782.0, 449.7), "s2_normal": (4513.5, 4513.5, 2073.5),
+                  "s2_flux": (25617.0, 25617.0, 2253.7), "s2_update": (272.0, 272.0, 1688.1)},
+}
 
 
 def parse():
@@ -125,11 +138,6 @@ class ClockSampler:
 def vortex_inputs(n, order, nq=4):
     from paper_2508_13705_gb300 import inputs
     return inputs.cell_state_2d(inputs.vortex_prim(), n, n, (0.0, 10.0, 0.0, 10.0), order, nq=nq)
-
-
-def face_points(n, order):
-    m = (order - 1) // 2
-    return 2 * (n + 1) * n * m
 
 
 def peaks():
@@ -259,19 +267,35 @@ def main():
     names_k = {0: "lines", 1: "normal", 2: "flux", 3: "update", 4: "dt"}
 
     def roof(prof, precision):
-        top = max(prof, key=lambda x: x[1])
-        kid, kms = top
-        total = sum(x[1] for x in prof)
-        fpp = FLOPS_PER_POINT.get((precision, order))
+        """Achieved FP rate of every kernel of the step against the FP pipe peak;
+        the headline entry is the kernel with the largest share of the step."""
+        counts = KERNEL_COUNTS.get((precision, order), {})
         peak = gpu_peak_tflops(precision, sm_count, mhz)
-        ach = None if fpp is None or kid % 10 != 2 else fpp * face_points(n, order) / (kms / 1e3) / 1e12
-        return {"bound": "alu", "kernel": "k_flux stage %d" % (kid // 10) if kid % 10 == 2 else names_k[kid % 10],
+        total = sum(x[1] for x in prof)
+        kms = {("s%d_" % (k // 10) if k >= 10 else "") + names_k[k % 10]: v for k, v in prof}
+        per = {}
+        for name, ms in kms.items():
+            if name not in counts:
+                continue
+            fl, _, by = counts[name]
+            ach = fl * cells / (ms / 1e3) / 1e12
+            per[name] = {"ms": round(ms, 4), "achieved_tflops": round(ach, 3), "frac": round(ach / peak, 4),
+                         "dram_gbs": round(by * cells / (ms / 1e3) / 1e9, 1)}
+        top = max(per, key=lambda k: per[k]["ms"]) if per else None
+        fl, _, by = counts[top] if top else (None, None, None)
+        ach = per[top]["achieved_tflops"] if top else None
+        return {"bound": "alu", "kernel": top,
                 "achieved": ach, "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": None if ach is None else ach / peak, "traffic": None,
-                "share_of_step": kms / total,
+                "frac": None if ach is None else ach / peak,
+                "traffic": None if by is None else round(by * cells),
+                "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum per cell on 1024^2, "
+                                 "times the launch's cells",
+                "flops_per_cell": fl,
+                "share_of_step": None if top is None else kms[top] / total,
                 "peak_basis": ("%d SMs x %d FP32 lanes x 2 x %.0f MHz" % (sm_count, FP32_PEAK_LANES, mhz))
                 if precision == "fp32" else "nominal FP64 1.25 TFLOP/s at 2070 MHz, scaled to %.0f MHz" % mhz,
-                "kernels_ms": {("s%d_" % (k // 10) if k >= 10 else "") + names_k[k % 10]: round(v, 4) for k, v in prof}}
+                "kernels": per,
+                "kernels_ms": {k: round(v, 4) for k, v in kms.items()}}
 
     line = {
         "metric": "Mcell-stage/s 2D 9th-order, FP32 form vs FP64 plain at fixed L1 err; %roofline",

@@ -98,8 +98,10 @@ int cgks_default_params(cgks_params* p, int dim, int order);
  * y bounds ignored).  All device buffers are allocated here on `stream`'s
  * device; the CUDA graph of one step is captured on first use.
  * Errors: CGKS_EINVAL (NULL out/p, dim not 1/2, order not 5/7/9, nx or ny < 1,
- * ny != 1 in 1-D, gamma <= 1, cfl <= 0, non-positive extent, FIXED bc in 2-D),
- * CGKS_ENOMEM, CGKS_ECUDA.  On error *out is NULL. */
+ * ny != 1 in 1-D, gamma <= 1, cfl <= 0, non-positive extent, FIXED bc in 2-D,
+ * a mesh with 2^31 or more face Gauss points: about 16000^2 cells at order 9,
+ * more than the device memory holds), CGKS_ENOMEM, CGKS_ECUDA.  On error *out
+ * is NULL. */
 int cgks_init_mesh(cgks_solver** out, const cgks_params* p, int nx, int ny,
                    double x0, double x1, double y0, double y1, void* stream);
 

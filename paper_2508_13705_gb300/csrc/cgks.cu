@@ -248,6 +248,9 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
     for (int k = 0; k < n; ++k) {
         if (nx[k] < 1 || ny[k] < 1 || (p->dim == 1 && ny[k] != 1)) return CGKS_EINVAL;
         if (!(ext[4 * k + 1] > ext[4 * k]) || (p->dim == 2 && !(ext[4 * k + 3] > ext[4 * k + 2]))) return CGKS_EINVAL;
+        // the kernels index a mesh's work items in 32 bits
+        for (int kind = 0; kind < W_COUNT; ++kind)
+            if (items(kind, p->dim, (p->order - 1) / 2, nx[k], ny[k]) >= (1LL << 31)) return CGKS_EINVAL;
     }
     if ((r = load_tables())) return r;
     cgks_batch* b = new (std::nothrow) cgks_batch();

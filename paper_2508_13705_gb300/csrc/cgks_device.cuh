@@ -385,6 +385,31 @@ __device__ __forceinline__ void recon(const DffR<R>& dff, int oi, int row0, cons
     recon_ao<R, NOUT>(dff.a, oi, row0, dp, out, ghi, glo, eps);
 }
 
+// The same with the order (table index OI) and the first output row fixed at
+// compile time, for the 2-D kernels, whose instantiation fixes the order: each
+// linear branch then takes its stencil row from a constant address, so the
+// coefficients enter the FMAs as constant-bank operands instead of loads.
+template <typename R, int NOUT, int OI, int ST, int ROW0>
+__device__ __forceinline__ void recon_lin(const R dp[10], R out[NOUT])
+{
+    const auto& T = Tab<R>::get(OI);
+#pragma unroll
+    for (int r = 0; r < NOUT; ++r) {
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) s += T.row[ST][ROW0 + r][k] * dp[k];
+        out[r] = s;
+    }
+}
+template <typename R, int NOUT, int OI, int ROW0>
+__device__ __forceinline__ void recon_k(const DffR<R>& dff, const R dp[10], R out[NOUT], R ghi, R glo, R eps)
+{
+    if (OI == 2 && dff.st == ST_R9) recon_lin<R, NOUT, OI, ST_R9, ROW0>(dp, out);
+    else if (OI >= 1 && dff.st == ST_R7) recon_lin<R, NOUT, OI, ST_R7, ROW0>(dp, out);
+    else if (dff.st == ST_R5) recon_lin<R, NOUT, OI, ST_R5, ROW0>(dp, out);
+    else recon_ao<R, NOUT>(dff.a, OI, ROW0, dp, out, ghi, glo, eps);
+}
+
 // ------------------------------------------------------------------ kinetics
 
 // Maxwellian moments per unit density for one velocity range, with the

@@ -88,15 +88,16 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
          gi += (long long)gridDim.x * blockDim.x) {
         int k = find_mesh(w, gi);
         const Mesh& g = w.mesh[k];
-        long long li = gi - w.off[k];
-        long long nxl = (long long)(g.nx + 6) * (g.ny + 2);
+        // local indices in 32 bits (the host bounds a mesh's work items below 2^31)
+        unsigned li = (unsigned)(gi - w.off[k]);
+        unsigned nxl = (unsigned)(g.nx + 6) * (unsigned)(g.ny + 2);
         int dir = li < nxl ? 0 : 1;
         if (dir == 1) li -= nxl;
         int na, nb;
         local_dims<M>(g, dir, na, nb);
         int a, b;
-        if (dir == 0) { a = (int)(li % (na + 6)) - 3; b = (int)(li / (na + 6)) - 1; }
-        else { b = (int)(li % (nb + 2)) - 1; a = (int)(li / (nb + 2)) - 3; }
+        if (dir == 0) { unsigned d = na + 6, q = li / d; a = (int)(li - q * d) - 3; b = (int)q - 1; }
+        else { unsigned d = nb + 2, q = li / d; b = (int)(li - q * d) - 1; a = (int)q - 3; }
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
         // the tangential stencil: a direct walk for interior cells, whose loads
         // are issued before the DFF selections so that their latencies overlap
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
                 dp[5 + q] = ht * swt[v][q];
             }
             R out[M];
-            recon<R, M>(dff, g.oi, 6, dp, out, (R)g.ghi, (R)g.glo, (R)g.eps);
+            recon_k<R, M, M - 2, 6>(dff, dp, out, (R)g.ghi, (R)g.glo, (R)g.eps);
 #pragma unroll
             for (int l = 0; l < M; ++l) res[l][v] = qi + out[l];
         }
@@ -177,19 +178,20 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
          gi += (long long)gridDim.x * blockDim.x) {
         int k = find_mesh(w, gi);
         const Mesh& g = w.mesh[k];
-        long long li = gi - w.off[k];
+        unsigned li = (unsigned)(gi - w.off[k]);  // 32-bit local index (bounded on the host)
         int dir = 0, na = g.nx, nb = 1;
         if (D == 2) {
-            long long nxl = (long long)(g.nx + 2) * (g.ny + 2) * M;
+            unsigned nxl = (unsigned)(g.nx + 2) * (unsigned)(g.ny + 2) * M;
             dir = li < nxl ? 0 : 1;
             if (dir == 1) li -= nxl;
             local_dims<M>(g, dir, na, nb);
         }
         int l = D == 2 ? (int)(li % M) : 0;
-        long long r = D == 2 ? li / M : li;
+        unsigned r = D == 2 ? li / M : li;
         int a, b;
-        if (dir == 0) { a = (int)(r % (na + 2)) - 1; b = D == 2 ? (int)(r / (na + 2)) - 1 : 0; }
-        else { b = (int)(r % (nb + 2)) - 1; a = (int)(r / (nb + 2)) - 1; }
+        if (D == 1) { a = (int)r - 1; b = 0; }
+        else if (dir == 0) { unsigned d = na + 2, q = r / d; a = (int)(r - q * d) - 1; b = (int)q - 1; }
+        else { unsigned d = nb + 2, q = r / d; b = (int)(r - q * d) - 1; a = (int)q - 1; }
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
         long long cidx = cell_idx(dir, na, nb, a, b);
         long long lstr = dir == 0 ? 1 : (nb + 2);  // LA stride between normal neighbours
@@ -264,7 +266,8 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
                 }
             }
             R out[6];
-            recon<R, 6>(dff, g.oi, 0, dp, out, (R)g.ghi, (R)g.glo, (R)g.eps);
+            if (D == 2) recon_k<R, 6, (M >= 2 ? M - 2 : 0), 0>(dff, dp, out, (R)g.ghi, (R)g.glo, (R)g.eps);
+            else recon<R, 6>(dff, g.oi, 0, dp, out, (R)g.ghi, (R)g.glo, (R)g.eps);
             R ih = (R)1 / hn;
             sideL[0][v] = qi + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
             sideR[0][v] = qi + out[3]; sideR[1][v] = out[4] * ih; sideR[2][v] = out[5] * ih * ih;
@@ -319,19 +322,20 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
          gi += (long long)gridDim.x * blockDim.x) {
         int k = find_mesh(w, gi);
         const Mesh& g = w.mesh[k];
-        long long li = gi - w.off[k];
+        unsigned li = (unsigned)(gi - w.off[k]);  // 32-bit local index (bounded on the host)
         int dir = 0, na = g.nx, nb = 1;
         if (D == 2) {
-            long long nxl = (long long)(g.nx + 1) * g.ny * M;
+            unsigned nxl = (unsigned)(g.nx + 1) * (unsigned)g.ny * M;
             dir = li < nxl ? 0 : 1;
             if (dir == 1) li -= nxl;
             local_dims<M>(g, dir, na, nb);
         }
         int l = D == 2 ? (int)(li % M) : 0;
-        long long r = D == 2 ? li / M : li;
+        unsigned r = D == 2 ? li / M : li;
         int f, b;
-        if (dir == 0) { f = (int)(r % (na + 1)); b = D == 2 ? (int)(r / (na + 1)) : 0; }
-        else { b = (int)(r % nb); f = (int)(r / nb); }
+        if (D == 1) { f = (int)r; b = 0; }
+        else if (dir == 0) { unsigned d = na + 1, q = r / d; f = (int)(r - q * d); b = (int)q; }
+        else { unsigned d = nb, q = r / d; b = (int)(r - q * d); f = (int)q; }
         const R* FR = (const R*)g.FR[dir];
         const R gm = MeshR<R>::gamma(g), K = MeshR<R>::K(g);
         const bool hgks = g.tau_mode == 1;
@@ -573,7 +577,8 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
         int k = find_mesh(w, gi);
         const Mesh& g = w.mesh[k];
         long long c = gi - w.off[k];
-        int i = (int)(c % g.nx), j = (int)(c / g.nx);
+        unsigned cu = (unsigned)c, qj = cu / (unsigned)g.nx;  // 32-bit (bounded on the host)
+        int i = (int)(cu - qj * (unsigned)g.nx), j = (int)qj;
         const R* FX = (const R*)g.FO[0];
         const R* FY = (const R*)g.FO[1];
         // x-faces: b = j, f = i and i+1; y-faces: b = i, f = j and j+1
