@@ -770,8 +770,12 @@ __global__ void __launch_bounds__(256) k_convert(Work w, int to_float)
 
 // -------------------------------------------------------------- CFL (Sec. 4)
 // max over cells of (|U| + a) / min(dx, dy); one atomicMax per block on the
-// bit pattern of a positive double (ordered like the value).
-template <int D>
+// bit pattern of a positive double (ordered like the value).  The plain form
+// evaluates the speeds in FP64 from the FP64 averages; the FP32-bulk form in
+// FP32 from its float state planes (the step size is not a conserved
+// quantity: its 1e-7 relative rounding only shifts where the steps fall),
+// and the maximum is taken in FP64 in both.
+template <int D, typename R>
 __global__ void __launch_bounds__(256) k_cfl(Work w)
 {
     __shared__ double red[8];
@@ -786,12 +790,16 @@ __global__ void __launch_bounds__(256) k_cfl(Work w)
         kprev = k;
         long long c = gi - w.off[k];
         long long P = g.plane;
-        double rho = g.S0[c], mu = g.S0[P + c] / rho;
-        double mv = D == 2 ? g.S0[2 * P + c] / rho : 0.0;
-        double E = g.S0[(D + 1) * P + c];
-        double p = (g.gamma - 1.0) * (E - 0.5 * rho * (mu * mu + mv * mv));
-        double h = D == 2 ? fmin(g.dx, g.dy) : g.dx;
-        double s = (sqrt(mu * mu + mv * mv) + sqrt(g.gamma * p / rho)) / h;
+        const R* S = state_planes<R>(g, 0);
+        const R gm = MeshR<R>::gamma(g);
+        R rho = S[c], ir = (R)1 / rho;
+        R mu = S[P + c] * ir;
+        R mv = D == 2 ? S[2 * P + c] * ir : (R)0;
+        R E = S[(D + 1) * P + c];
+        R q2 = mu * mu + mv * mv;
+        R p = (gm - (R)1) * (E - (R)0.5 * rho * q2);
+        R ih = D == 2 ? fmax(MeshR<R>::ih(g, 0), MeshR<R>::ih(g, 1)) : MeshR<R>::ih(g, 0);  // 1 / min(dx, dy)
+        double s = (double)((sqrt(q2) + sqrt(gm * p * ir)) * ih);
         if (!(s == s)) s = 1e300;  // a NaN state yields a tiny step and is flagged by the stages
         best = fmax(best, s);
     }

@@ -27,7 +27,7 @@ Kfns make_kfns()
     k.flux2 = k.flux2v[0];
     if (D == 2) { k.upd1 = (KOne)k_update2<M, R, 1>; k.upd2 = (KOne)k_update2<M, R, 2>; }
     else { k.upd1 = (KOne)k_update1<R, 1>; k.upd2 = (KOne)k_update1<R, 2>; }
-    k.cfl = k_cfl<D>;
+    k.cfl = k_cfl<D, R>;
     k.siginit = k_sigma_init<D>;
     k.check = k_check_state<D>;
     k.convert = k_convert<D, M>;
