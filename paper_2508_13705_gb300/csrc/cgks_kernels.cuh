@@ -10,9 +10,13 @@
 // normal; M Gauss points per face).  Direction 0 as written; direction 1 with
 // the two spatial indices swapped, so the global x index is always fastest:
 //   LA  [nb+2][na+6][M][4]            line averages, b in [-1, nb], a in [-3, na+2]
-//   FR  [nb+2][na+1][M][2][3][4]      face states: side 0 = left (from cell f-1),
-//                                     side 1 = right (from cell f); W, W_n, W_nn
-//   FO  [nb][na+1][M][16]             per-point stage outputs (global frame)
+//   FR  [2]{[nb+2][na+1][M][8], [nb+2][na+1][M][4]}
+//                                     face states: side 0 = left (from cell f-1),
+//                                     side 1 = right (from cell f); per side one
+//                                     plane of (W, W_n) pairs, which Step 3 reads
+//                                     together, and one plane of W_nn
+//   FO  [4][M][nb][na+1][4]           per-point stage outputs (global frame),
+//                                     one plane per output quantity and line
 //   SP  [nb][na+1][M]                 sigma per face Gauss point (Eq. 3.2)
 //   AT  [nb+2][na+6]                  tangential r5 DFF of each cell (Step 3)
 //   DN  [nb+2][na+6][4]               normal-direction DFF of each cell (Step 2), packed
@@ -72,6 +76,17 @@ __device__ __forceinline__ long long fr_row(int dir, int na, int nb, int bb, int
 __device__ __forceinline__ long long pt_idx(int dir, int na, int nb, int b, int f)
 {
     return dir == 0 ? (long long)b * (na + 1) + f : (long long)f * nb + b;
+}
+// element offsets of a 16-byte group: FR (point = fr_row * M + l, npt points a
+// side) and FO (face = pt_idx, nf faces a plane)
+__device__ __forceinline__ long long fr_npt(int na, int nb, int M) { return (long long)(nb + 2) * (na + 1) * M; }
+__device__ __forceinline__ long long fr_off(long long npt, long long pt, int side, int nd)
+{
+    return side * npt * 12 + (nd < 2 ? pt * 8 + nd * 4 : npt * 8 + pt * 4);
+}
+__device__ __forceinline__ long long fo_off(long long nf, int M, int q, int l, long long face)
+{
+    return ((long long)(q * M + l) * nf + face) * 4;
 }
 
 __device__ __forceinline__ void flag_bad(const Mesh& g, long long idx)
@@ -276,17 +291,18 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
 #pragma unroll
             for (int nd = 0; nd < 3; ++nd) { sideL[nd][3] = (R)0; sideR[nd][3] = (R)0; }
         }
+        const long long npt = fr_npt(na, nb, M);
         // side 0: left state of face a+1 (value at xi = +1/2)
         if (a + 1 <= na) {
-            R* fr = FR + ((fr_row(dir, na, nb, b + 1, a + 1) * M + l) * 2 + 0) * 12;
+            long long pt = fr_row(dir, na, nb, b + 1, a + 1) * M + l;
 #pragma unroll
-            for (int nd = 0; nd < 3; ++nd) st4(fr + nd * 4, sideL[nd]);
+            for (int nd = 0; nd < 3; ++nd) st4(FR + fr_off(npt, pt, 0, nd), sideL[nd]);
         }
         // side 1: right state of face a (value at xi = -1/2)
         if (a >= 0) {
-            R* fr = FR + ((fr_row(dir, na, nb, b + 1, a) * M + l) * 2 + 1) * 12;
+            long long pt = fr_row(dir, na, nb, b + 1, a) * M + l;
 #pragma unroll
-            for (int nd = 0; nd < 3; ++nd) st4(fr + nd * 4, sideR[nd]);
+            for (int nd = 0; nd < 3; ++nd) st4(FR + fr_off(npt, pt, 1, nd), sideR[nd]);
         }
     }
     __syncthreads();
@@ -353,9 +369,15 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         for (int side = 0; side < 2; ++side) {
             // Step 2 data: W, W_n, W_nn
             R d[6][4];
-            const R* fr = FR + ((fr_row(dir, na, nb, b + 1, f) * M + l) * 2 + side) * 12;
-#pragma unroll
-            for (int nd = 0; nd < 3; ++nd) ld4(fr + nd * 4, d[nd]);
+            // this side's W plane and the row stride of the tangential segments
+            // (FR point of segment b + s, line kk: p00 + s * rs + kk)
+            const long long npt = fr_npt(na, nb, M);
+            const long long p00 = fr_row(dir, na, nb, b, f) * M;
+            const R* Fs = FR + side * npt * 12 + p00 * 8;                 // (W, W_n) of segment b - 1
+            const long long rs = (dir == 0 ? (long long)(na + 1) : 1LL) * M;
+            ld4(Fs + (rs + l) * 8, d[0]);
+            ld4(Fs + (rs + l) * 8 + 4, d[1]);
+            ld4(FR + side * npt * 12 + npt * 8 + (p00 + rs + l) * 4, d[2]);
             if (D == 2) {
                 // Step 3: tangential derivatives from the 3M face points of
                 // segments b-1, b, b+1, scaled by the tangential r5 DFF of the
@@ -369,7 +391,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
                 for (int s = 0; s < 3; ++s)
 #pragma unroll
                     for (int kk = 0; kk < M; ++kk) {
-                        const R* q = FR + ((fr_row(dir, na, nb, b + s, f) * M + kk) * 2 + side) * 12;
+                        const R* q = Fs + (s * rs + kk) * 8;
                         R x0[4], x1[4];
                         ld4(q, x0);
                         ld4(q + 4, x1);
@@ -534,8 +556,10 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
                 Wtt[v] += (R)4 * (ed - eh) / Dt * dS;
             }
         }
-        long long pt = pt_idx(dir, na, nb, b, f) * M + l;
-        R* FO = (R*)g.FO[dir] + pt * 16;
+        long long face = pt_idx(dir, na, nb, b, f);
+        long long pt = face * M + l;  // SP index
+        const long long nf = (long long)nb * (na + 1);
+        R* FO = (R*)g.FO[dir];
         R o[4][4];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
@@ -557,7 +581,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         for (int q = 0; q < NO; ++q) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) finite &= isfinite(o[q][v]);
-            st4(FO + q * 4, o[q]);
+            st4(FO + fo_off(nf, M, q, l, face), o[q]);
         }
         if (STAGE == 1) g.SP[dir][pt] = sig;
         if (bad || !ok || !finite) flag_bad(g, pt);
@@ -582,10 +606,8 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
         const R* FX = (const R*)g.FO[0];
         const R* FY = (const R*)g.FO[1];
         // x-faces: b = j, f = i and i+1; y-faces: b = i, f = j and j+1
-        const R* xl = FX + (((long long)j * (g.nx + 1) + i) * M) * 16;
-        const R* xr = xl + M * 16;
-        const R* yl = FY + (((long long)j * g.nx + i) * M) * 16;
-        const R* yr = yl + (long long)g.nx * M * 16;
+        const long long fxl = (long long)j * (g.nx + 1) + i, fyl = (long long)j * g.nx + i;
+        const long long nfx = (long long)g.ny * (g.nx + 1), nfy = (long long)g.nx * (g.ny + 1);
         const double idx = g.idx, idy = g.idy;
         const R ridx = MeshR<R>::ih(g, 0), ridy = MeshR<R>::ih(g, 1);
         long long P = g.plane;
@@ -607,10 +629,10 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
             // stage 2: o0 = dt^2/3 F_t*, o1 = dt^2/3 W_tt*
 #pragma unroll
             for (int q = 0; q < (STAGE == 1 ? 4 : 2); ++q) {
-                ld4(xr + l * 16 + q * 4, a);
-                ld4(xl + l * 16 + q * 4, bq);
-                ld4(yr + l * 16 + q * 4, cq);
-                ld4(yl + l * 16 + q * 4, dq);
+                ld4(FX + fo_off(nfx, M, q, l, fxl + 1), a);
+                ld4(FX + fo_off(nfx, M, q, l, fxl), bq);
+                ld4(FY + fo_off(nfy, M, q, l, fyl + g.nx), cq);
+                ld4(FY + fo_off(nfy, M, q, l, fyl), dq);
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     R dx_ = a[v] - bq[v];
@@ -706,8 +728,10 @@ __global__ void __launch_bounds__(256) k_update1(Work w)
         const Mesh& g = w.mesh[k];
         int i = (int)(gi - w.off[k]);
         const R* FX = (const R*)g.FO[0];
-        const R* xl = FX + (long long)i * 16;
-        const R* xr = xl + 16;
+        // q-th output quantity of variable v at face i (left) or i + 1 (right)
+        const long long nf = g.nx + 1;
+        auto xl = [&](int e) { return FX[fo_off(nf, 1, e >> 2, 0, i) + (e & 3)]; };
+        auto xr = [&](int e) { return FX[fo_off(nf, 1, e >> 2, 0, i + 1) + (e & 3)]; };
         const double idx = g.idx;
         long long P = g.plane;
         bool bad = false;
@@ -715,14 +739,14 @@ __global__ void __launch_bounds__(256) k_update1(Work w)
             double Wn, Sn;
             if (STAGE == 1) {
                 double W = g.S0[v * P + i];
-                Wn = W - ((double)xr[v] - (double)xl[v]) * idx;
-                Sn = ((double)xr[8 + v] - (double)xl[8 + v]) * idx;
+                Wn = W - ((double)xr(v) - (double)xl(v)) * idx;
+                Sn = ((double)xr(8 + v) - (double)xl(8 + v)) * idx;
                 g.S1[v * P + i] = Wn;
-                g.ACC[v * P + i] = W - ((double)xr[4 + v] - (double)xl[4 + v]) * idx;
-                g.ACC[(3 + v) * P + i] = ((double)xr[12 + v] - (double)xl[12 + v]) * idx;
+                g.ACC[v * P + i] = W - ((double)xr(4 + v) - (double)xl(4 + v)) * idx;
+                g.ACC[(3 + v) * P + i] = ((double)xr(12 + v) - (double)xl(12 + v)) * idx;
             } else {
-                Wn = g.ACC[v * P + i] - ((double)xr[v] - (double)xl[v]) * idx;
-                Sn = g.ACC[(3 + v) * P + i] + ((double)xr[4 + v] - (double)xl[4 + v]) * idx;
+                Wn = g.ACC[v * P + i] - ((double)xr(v) - (double)xl(v)) * idx;
+                Sn = g.ACC[(3 + v) * P + i] + ((double)xr(4 + v) - (double)xl(4 + v)) * idx;
                 g.S0[v * P + i] = Wn;
             }
             if (BULK32) {
