@@ -401,6 +401,30 @@ __device__ __forceinline__ void recon_lin(const R dp[10], R out[NOUT])
         out[r] = s;
     }
 }
+// Compile-time stencil tag (-1: HWENO-AO) for branch-hoisted reconstruction
+// loops: the branch on a cell's stencil is taken once, outside the loop over
+// variables, so each branch is one straight run of code.
+template <int V> struct StTag { static constexpr int value = V; };
+
+// Reconstruction with the stencil fixed at compile time (ST = -1: HWENO-AO).
+template <typename R, int NOUT, int OI, int ST, int ROW0>
+__device__ __forceinline__ void recon_st(const DffR<R>& dff, const R dp[10], R out[NOUT], R ghi, R glo, R eps)
+{
+    if constexpr (ST >= 0) recon_lin<R, NOUT, OI, ST, ROW0>(dp, out);
+    else recon_ao<R, NOUT>(dff.a, OI, ROW0, dp, out, ghi, glo, eps);
+}
+
+// Calls body(StTag<st>()) for the stencil of dff; the order (table index OI)
+// bounds the linear stencils that can occur.
+template <int OI, typename R, typename Body>
+__device__ __forceinline__ void with_stencil(const DffR<R>& dff, Body&& body)
+{
+    if (OI == 2 && dff.st == ST_R9) body(StTag<(OI == 2 ? ST_R9 : ST_R5)>());
+    else if (OI >= 1 && dff.st == ST_R7) body(StTag<(OI >= 1 ? ST_R7 : ST_R5)>());
+    else if (dff.st == ST_R5) body(StTag<ST_R5>());
+    else body(StTag<-1>());
+}
+
 template <typename R, int NOUT, int OI, int ROW0>
 __device__ __forceinline__ void recon_k(const DffR<R>& dff, const R dp[10], R out[NOUT], R ghi, R glo, R eps)
 {

@@ -162,19 +162,23 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
             st4((R*)g.DN[dir] + cidx * 4, pk);
         }
         R res[M][4];
+        const R ghi = (R)g.ghi, glo = (R)g.glo, eps = (R)g.eps;
+        with_stencil<M - 2>(dff, [&](auto tag) {
+            constexpr int ST = decltype(tag)::value;
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            R qi = sw[v][2], dp[10];
+            for (int v = 0; v < 4; ++v) {
+                R qi = sw[v][2], dp[10];
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                dp[q] = sw[v][q] - qi;
-                dp[5 + q] = ht * swt[v][q];
+                for (int q = 0; q < 5; ++q) {
+                    dp[q] = sw[v][q] - qi;
+                    dp[5 + q] = ht * swt[v][q];
+                }
+                R out[M];
+                recon_st<R, M, M - 2, ST, 6>(dff, dp, out, ghi, glo, eps);
+#pragma unroll
+                for (int l = 0; l < M; ++l) res[l][v] = qi + out[l];
             }
-            R out[M];
-            recon_k<R, M, M - 2, 6>(dff, dp, out, (R)g.ghi, (R)g.glo, (R)g.eps);
-#pragma unroll
-            for (int l = 0; l < M; ++l) res[l][v] = qi + out[l];
-        }
+        });
 #pragma unroll
         for (int l = 0; l < M; ++l) st4(LA + l * 4, res[l]);
     }
@@ -262,30 +266,40 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
                     for (int q = 0; q < 5; ++q) sl[v][q] = lcell<2, M, R>(g, S, dir, 3, v, l, a + q - 2, b);
             }
         }
+        const R ghi = (R)g.ghi, glo = (R)g.glo, eps = (R)g.eps;
+        const R ih = (R)1 / hn;
+        if constexpr (D == 2) {
+            with_stencil<(M >= 2 ? M - 2 : 0)>(dff, [&](auto tag) {
+                constexpr int ST = decltype(tag)::value;
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            R qi;
-            R dp[10];
-            if (D == 2) {
-                qi = la5[2][v];
+                for (int v = 0; v < NV; ++v) {
+                    R qi = la5[2][v], dp[10];
 #pragma unroll
-                for (int q = 0; q < 5; ++q) dp[q] = la5[q][v] - qi;
+                    for (int q = 0; q < 5; ++q) {
+                        dp[q] = la5[q][v] - qi;
+                        dp[5 + q] = hn * sl[v][q];
+                    }
+                    R out[6];
+                    recon_st<R, 6, (M >= 2 ? M - 2 : 0), ST, 0>(dff, dp, out, ghi, glo, eps);
+                    sideL[0][v] = qi + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
+                    sideR[0][v] = qi + out[3]; sideR[1][v] = out[4] * ih; sideR[2][v] = out[5] * ih * ih;
+                }
+            });
+        } else {
 #pragma unroll
-                for (int q = 0; q < 5; ++q) dp[5 + q] = hn * sl[D == 2 ? v : 0][q];
-            } else {
-                qi = cell<1, 1, R>(g, S, 0, v, 0, a, 0);
+            for (int v = 0; v < NV; ++v) {
+                R qi = cell<1, 1, R>(g, S, 0, v, 0, a, 0);
+                R dp[10];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
                     dp[q] = cell<1, 1, R>(g, S, 0, v, 0, a + q - 2, 0) - qi;
                     dp[5 + q] = hn * cell<1, 1, R>(g, S, 1, v, 0, a + q - 2, 0);
                 }
+                R out[6];
+                recon<R, 6>(dff, g.oi, 0, dp, out, ghi, glo, eps);
+                sideL[0][v] = qi + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
+                sideR[0][v] = qi + out[3]; sideR[1][v] = out[4] * ih; sideR[2][v] = out[5] * ih * ih;
             }
-            R out[6];
-            if (D == 2) recon_k<R, 6, (M >= 2 ? M - 2 : 0), 0>(dff, dp, out, (R)g.ghi, (R)g.glo, (R)g.eps);
-            else recon<R, 6>(dff, g.oi, 0, dp, out, (R)g.ghi, (R)g.glo, (R)g.eps);
-            R ih = (R)1 / hn;
-            sideL[0][v] = qi + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
-            sideR[0][v] = qi + out[3]; sideR[1][v] = out[4] * ih; sideR[2][v] = out[5] * ih * ih;
         }
         if (D == 1) {
 #pragma unroll
