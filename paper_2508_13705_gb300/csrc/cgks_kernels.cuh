@@ -9,7 +9,7 @@
 // Scratch layouts per mesh and direction (na, nb: cells along / across the
 // normal; M Gauss points per face).  Direction 0 as written; direction 1 with
 // the two spatial indices swapped, so the global x index is always fastest:
-//   LA  [nb+2][na+6][M][4]            line averages, b in [-1, nb], a in [-3, na+2]
+//   LA  [M][nb+2][na+6][4]            line averages, b in [-1, nb], a in [-3, na+2]
 //   FR  [2]{[nb+2][na+1][M][8], [nb+2][na+1][M][4]}
 //                                     face states: side 0 = left (from cell f-1),
 //                                     side 1 = right (from cell f); per side one
@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         DffR<R> dff = dff_r<R>(dff_select(g.order, s6, g.thr));
         R ht = (R)(dir == 0 ? g.dy : g.dx);
         long long cidx = cell_idx(dir, na, nb, a, b);
-        R* LA = (R*)g.LA[dir] + cidx * M * 4;
+        const long long ncell = (long long)(nb + 2) * (na + 6);  // cells of one LA plane
+        R* LA = (R*)g.LA[dir] + cidx * 4;
         // tangential r5 DFF of this cell, reused by Step 3 in k_flux
         ((R*)g.AT[dir])[cidx] = (R)dff.a[3];
         // normal-direction DFF of this cell, reused by every Gauss line in k_normal
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
             }
         });
 #pragma unroll
-        for (int l = 0; l < M; ++l) st4(LA + l * 4, res[l]);
+        for (int l = 0; l < M; ++l) st4(LA + l * ncell * 4, res[l]);
     }
 }
 
@@ -237,9 +238,9 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         // the line averages of the five stencil cells on this Gauss line
         R la5[5][4];
         if (D == 2) {
-            const R* la = (const R*)g.LA[dir] + cidx * M * 4 + l * 4;
+            const R* la = (const R*)g.LA[dir] + ((long long)l * (nb + 2) * (na + 6) + cidx) * 4;
 #pragma unroll
-            for (int q = 0; q < 5; ++q) ld4(la + (q - 2) * lstr * M * 4, la5[q]);
+            for (int q = 0; q < 5; ++q) ld4(la + (q - 2) * lstr * 4, la5[q]);
         }
         R sideL[3][4], sideR[3][4];
         // the normal stencil of line slopes: a direct walk for interior cells
@@ -604,8 +605,8 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
 
 // -------------------------------------------------------------- update (2-D)
 // Stage 1 writes W* (S1) and the accumulator; stage 2 writes state n+1 (S0).
-// FP32-bulk form: the FP64 planes receive the cell averages, the float planes
-// (F1 / F0) everything the next stage reads.
+// FP32-bulk form: the float planes (F1 / F0) receive everything the next stage
+// reads, the FP64 planes the cell averages of state n+1 (W* lives in F1 only).
 template <int M, typename R, int STAGE>
 __global__ void __launch_bounds__(256) k_update2(Work w)
 {
@@ -690,7 +691,8 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
             } else {
                 Wn = g.ACC[v * P + c] - (double)fx0[v] * idx - (double)fy0[v] * idy;  // Eq. 2.22-2.23
             }
-            out[v * P + c] = Wn;
+            // the FP32-bulk stage 2 reads W* from the float planes only
+            if (!BULK32 || STAGE == 2) out[v * P + c] = Wn;
             bad |= !isfinite(Wn);
             if (BULK32) {
                 outf[v * P + c] = (float)Wn;
@@ -755,7 +757,7 @@ __global__ void __launch_bounds__(256) k_update1(Work w)
                 double W = g.S0[v * P + i];
                 Wn = W - ((double)xr(v) - (double)xl(v)) * idx;
                 Sn = ((double)xr(8 + v) - (double)xl(8 + v)) * idx;
-                g.S1[v * P + i] = Wn;
+                if (!BULK32) g.S1[v * P + i] = Wn;  // the FP32-bulk stage 2 reads the float planes
                 g.ACC[v * P + i] = W - ((double)xr(4 + v) - (double)xl(4 + v)) * idx;
                 g.ACC[(3 + v) * P + i] = ((double)xr(12 + v) - (double)xl(12 + v)) * idx;
             } else {
