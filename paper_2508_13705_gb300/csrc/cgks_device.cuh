@@ -537,165 +537,64 @@ __device__ __forceinline__ void slope(const Mom<R, D>& M, R K, const R* b, R* a)
     }
 }
 
-// Reconstructed data on one side of a face point, local frame (n normal, t
-// tangential, momentum components ordered normal first):
-// 0 W, 1 W_n, 2 W_nn, 3 W_t, 4 W_tt, 5 W_nt
+// Moments linear in the micro-slope: <a u^p v^q psi> = sum_k a_k G[k][i] with
+// the symmetric Gram matrix G[k][i] = <u^p v^q psi_k psi_i> per unit density.
+// A matrix serves every product with the same (p, q) and Maxwellian, which
+// costs a 4 x 4 multiply instead of a moment expansion each.  Stored as the
+// upper triangle: 2-D (00 01 02 03 11 12 13 22 23 33), 1-D (00 01 02 11 12 22).
 template <typename R, int D>
-struct SideData { R d[6][4]; };
+struct Gram { R g[D == 2 ? 10 : 6]; };
 
-// Per-point results in the local frame: F, F_t (fitted flux and derivative,
-// Eq. 2.19-2.20), Q0 = W(0), W_t, W_tt (Eq. 2.29).  Returns false on a
-// non-positive density / pressure.
-template <typename R, int D>
-__device__ __forceinline__ bool kinetic(const SideData<R, D>& L, const SideData<R, D>& Rt, R gamma, R K,
-                                        int tau_mode, R c1, R c2, R dt,
-                                        R F[4], R Ft[4], R Q0[4], R Wt[4], R Wtt[4])
+template <typename R, int D, int P, int Q>
+__device__ __forceinline__ void gram(const Mom<R, D>& M, Gram<R, D>& G)
 {
-    constexpr int NV = D + 2;
-    constexpr int ND = D == 2 ? 5 : 2;
-    Mom<R, D> Ml, Mr, M0;
-    bool ok = maxwellian<R, D>(L.d[0], gamma, K, 1, Ml);
-    ok &= maxwellian<R, D>(Rt.d[0], gamma, K, 2, Mr);
-    // kinetic weighting of the initial states (Eq. 2.7)
-    R e1[4] = {1, 0, 0, 0};
-    R tl[4], tr[4];
-    mom<R, D>(Ml, e1, 0, 0, tl);
-    mom<R, D>(Mr, e1, 0, 0, tr);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) Q0[i] = Ml.rho * tl[i] + Mr.rho * tr[i];
-    R dQ[ND][4];
-    R al_n[4], al_t[4], ar_n[4], ar_t[4];
-#pragma unroll
-    for (int q = 0; q < ND; ++q) {
-        R a_l[4], a_r[4];
-        slope<R, D>(Ml, K, L.d[q + 1], a_l);
-        slope<R, D>(Mr, K, Rt.d[q + 1], a_r);
-        if (q == 0) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) { al_n[i] = a_l[i]; ar_n[i] = a_r[i]; }
-        }
-        if (D == 2 && q == 2) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) { al_t[i] = a_l[i]; ar_t[i] = a_r[i]; }
-        }
-        mom<R, D>(Ml, a_l, 0, 0, tl);
-        mom<R, D>(Mr, a_r, 0, 0, tr);
-#pragma unroll
-        for (int i = 0; i < NV; ++i) dQ[q][i] = Ml.rho * tl[i] + Mr.rho * tr[i];
-    }
-    ok &= maxwellian<R, D>(Q0, gamma, K, 0, M0);
-    // equilibrium micro-slopes: n, nn (, t, tt, nt)
-    R ab[ND][4];
-#pragma unroll
-    for (int q = 0; q < ND; ++q) slope<R, D>(M0, K, dQ[q], ab[q]);
-    R S1[4], S2[4], z[4], rhs[4], Ab[4], A1t[4], A2t[4] = {0, 0, 0, 0};
-    // S1 = <a_n u + a_t v>, A-bar from <a_n u + a_t v + A> = 0
-    mom<R, D>(M0, ab[0], 1, 0, S1);
+    const R* m = M.mu + P;
     if (D == 2) {
-        mom<R, D>(M0, ab[2], 0, 1, z);
-#pragma unroll
-        for (int i = 0; i < NV; ++i) S1[i] += z[i];
+        const R* v = M.mv + Q;
+        G.g[0] = m[0] * v[0];
+        G.g[1] = m[1] * v[0];
+        G.g[2] = m[0] * v[1];
+        G.g[3] = (R)0.5 * (m[2] * v[0] + m[0] * v[2] + M.x2 * G.g[0]);
+        G.g[4] = m[2] * v[0];
+        G.g[5] = m[1] * v[1];
+        G.g[6] = (R)0.5 * (m[3] * v[0] + m[1] * v[2] + M.x2 * G.g[1]);
+        G.g[7] = m[0] * v[2];
+        G.g[8] = (R)0.5 * (m[2] * v[1] + m[0] * v[3] + M.x2 * G.g[2]);
+        G.g[9] = (R)0.25 * (m[4] * v[0] + m[0] * v[4] + M.x4 * G.g[0]
+                            + (R)2 * (m[2] * v[2] + M.x2 * (G.g[4] + G.g[7])));
+    } else {
+        G.g[0] = m[0];
+        G.g[1] = m[1];
+        G.g[2] = (R)0.5 * (m[2] + M.x2 * m[0]);
+        G.g[3] = m[2];
+        G.g[4] = (R)0.5 * (m[3] + M.x2 * m[1]);
+        G.g[5] = (R)0.25 * (m[4] + (R)2 * M.x2 * m[2] + M.x4 * m[0]);
     }
-#pragma unroll
-    for (int i = 0; i < NV; ++i) { S1[i] *= M0.rho; rhs[i] = -S1[i]; }
-    slope<R, D>(M0, K, rhs, Ab);
-    // time derivatives of the slopes, <a_nn u + a_nt v + a_1t> = 0 etc.
-    mom<R, D>(M0, ab[1], 1, 0, rhs);
+}
+
+// out_i = s * sum_k a_k G[k][i]
+template <typename R, int D>
+__device__ __forceinline__ void gmul(const Gram<R, D>& G, const R* a, R s, R* out)
+{
     if (D == 2) {
-        mom<R, D>(M0, ab[4], 0, 1, z);
-#pragma unroll
-        for (int i = 0; i < NV; ++i) rhs[i] += z[i];
+        const R* g = G.g;
+        out[0] = s * (a[0] * g[0] + a[1] * g[1] + a[2] * g[2] + a[3] * g[3]);
+        out[1] = s * (a[0] * g[1] + a[1] * g[4] + a[2] * g[5] + a[3] * g[6]);
+        out[2] = s * (a[0] * g[2] + a[1] * g[5] + a[2] * g[7] + a[3] * g[8]);
+        out[3] = s * (a[0] * g[3] + a[1] * g[6] + a[2] * g[8] + a[3] * g[9]);
+    } else {
+        const R* g = G.g;
+        out[0] = s * (a[0] * g[0] + a[1] * g[1] + a[2] * g[2]);
+        out[1] = s * (a[0] * g[1] + a[1] * g[3] + a[2] * g[4]);
+        out[2] = s * (a[0] * g[2] + a[1] * g[4] + a[2] * g[5]);
     }
-#pragma unroll
-    for (int i = 0; i < NV; ++i) rhs[i] *= -M0.rho;
-    slope<R, D>(M0, K, rhs, A1t);
-    if (D == 2) {
-        mom<R, D>(M0, ab[4], 1, 0, rhs);
-        mom<R, D>(M0, ab[3], 0, 1, z);
-#pragma unroll
-        for (int i = 0; i < NV; ++i) rhs[i] = -M0.rho * (rhs[i] + z[i]);
-        slope<R, D>(M0, K, rhs, A2t);
-    }
-    // S2 = <a_1t u + a_2t v>
-    mom<R, D>(M0, A1t, 1, 0, S2);
-    if (D == 2) {
-        mom<R, D>(M0, A2t, 0, 1, z);
-#pragma unroll
-        for (int i = 0; i < NV; ++i) S2[i] += z[i];
-    }
-#pragma unroll
-    for (int i = 0; i < NV; ++i) S2[i] *= M0.rho;
-    // flux terms: <u> and <A u> (equilibrium part, linear in t)
-    R T0[4], T1[4];
-    mom<R, D>(M0, e1, 1, 0, T0);
-    mom<R, D>(M0, Ab, 1, 0, T1);
-#pragma unroll
-    for (int i = 0; i < NV; ++i) {
-        T0[i] *= M0.rho;
-        T1[i] *= M0.rho;
-        F[i] = T0[i];
-        Ft[i] = T1[i];
-        Wt[i] = -S1[i];
-        Wtt[i] = -S2[i];
-    }
-    if (tau_mode == 1) {
-        R pl = (gamma - (R)1) * (L.d[0][NV - 1] - (R)0.5 * Ml.rho * (Ml.U * Ml.U + Ml.V * Ml.V));
-        R pr = (gamma - (R)1) * (Rt.d[0][NV - 1] - (R)0.5 * Mr.rho * (Mr.U * Mr.U + Mr.V * Mr.V));
-        R tau = c1 * dt + c2 * fabs(pl - pr) / (pl + pr) * dt;
-        // non-equilibrium and collision terms of Eq. 2.6
-        R Att[4], T2[4], T3[4], T4[4], T5[4], T6[4], S1h[4];
-#pragma unroll
-        for (int i = 0; i < NV; ++i) rhs[i] = -S2[i];
-        slope<R, D>(M0, K, rhs, Att);
-        mom<R, D>(M0, Att, 1, 0, T2);
-        mom<R, D>(M0, ab[0], 2, 0, T3);
-        mom<R, D>(M0, A1t, 2, 0, T4);
-        if (D == 2) {
-            mom<R, D>(M0, ab[2], 1, 1, z);
-#pragma unroll
-            for (int i = 0; i < NV; ++i) T3[i] += z[i];
-            mom<R, D>(M0, A2t, 1, 1, z);
-#pragma unroll
-            for (int i = 0; i < NV; ++i) T4[i] += z[i];
-        }
-        mom<R, D>(Ml, e1, 1, 0, tl);
-        mom<R, D>(Mr, e1, 1, 0, tr);
-#pragma unroll
-        for (int i = 0; i < NV; ++i) T5[i] = Ml.rho * tl[i] + Mr.rho * tr[i];
-        // half-range slope terms, with and without the extra u of the flux
-        R hl[4], hr[4];
-        for (int pu = 0; pu < 2; ++pu) {
-            mom<R, D>(Ml, al_n, pu + 1, 0, tl);
-            mom<R, D>(Mr, ar_n, pu + 1, 0, tr);
-            if (D == 2) {
-                mom<R, D>(Ml, al_t, pu, 1, hl);
-                mom<R, D>(Mr, ar_t, pu, 1, hr);
-#pragma unroll
-                for (int i = 0; i < NV; ++i) { tl[i] += hl[i]; tr[i] += hr[i]; }
-            }
-#pragma unroll
-            for (int i = 0; i < NV; ++i) {
-                R s = Ml.rho * tl[i] + Mr.rho * tr[i];
-                if (pu == 0) S1h[i] = s; else T6[i] = s;
-            }
-        }
-        R ed = exp(-dt / tau), eh = exp((R)-0.5 * dt / tau);
-        R h = (R)0.5 * dt;
-        R E0d = tau * ((R)1 - ed), E0h = tau * ((R)1 - eh);
-        R E1d = tau * tau * ((R)1 - ed) - tau * dt * ed, E1h = tau * tau * ((R)1 - eh) - tau * h * eh;
-        R f0 = ((R)4 * E0h - E0d) / dt, g0 = (R)4 * (E0d - (R)2 * E0h) / (dt * dt);
-        R f1 = ((R)4 * E1h - E1d) / dt, g1 = (R)4 * (E1d - (R)2 * E1h) / (dt * dt);
-#pragma unroll
-        for (int i = 0; i < NV; ++i) {
-            R T3s = T3[i] * M0.rho, T4s = T4[i] * M0.rho, T2s = T2[i] * M0.rho;
-            F[i] = T0[i] * ((R)1 - f0) - tau * T1[i] + (f1 - tau) * T3s + f0 * T5[i] - f1 * T6[i];
-            Ft[i] = -g0 * T0[i] + T1[i] - tau * T2s + g1 * T3s - tau * T4s + g0 * T5[i] - g1 * T6[i];
-            R dS = S1[i] - S1h[i];
-            Wt[i] += ((R)2 * eh - ed) * dS;
-            Wtt[i] += (R)4 * (ed - eh) / dt * dS;
-        }
-    }
-    return ok;
+}
+// row 0 of G (the product with a = e_0), times s
+template <typename R, int D>
+__device__ __forceinline__ void grow0(const Gram<R, D>& G, R s, R* out)
+{
+    if (D == 2) { out[0] = s * G.g[0]; out[1] = s * G.g[1]; out[2] = s * G.g[2]; out[3] = s * G.g[3]; }
+    else { out[0] = s * G.g[0]; out[1] = s * G.g[1]; out[2] = s * G.g[2]; }
 }
 
 } // namespace cgks

@@ -441,10 +441,12 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
             // kinetic weighting (Eq. 2.7): this side's half-range integrals
             Mom<R, D> Ms;
             ok &= maxwellian<R, D>(d[0], gm, K, side == 0 ? 1 : 2, Ms);
+            Gram<R, D> Gs;  // half-range <psi psi> of this side
+            gram<R, D, 0, 0>(Ms, Gs);
             R t[4], z[4];
-            mom<R, D>(Ms, e1, 0, 0, t);
+            grow0<R, D>(Gs, Ms.rho, t);
 #pragma unroll
-            for (int v = 0; v < NV; ++v) Q0[v] += Ms.rho * t[v];
+            for (int v = 0; v < NV; ++v) Q0[v] += t[v];
             if (hgks) {
                 mom<R, D>(Ms, e1, 1, 0, t);
 #pragma unroll
@@ -454,9 +456,9 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
             for (int q = 0; q < ND; ++q) {
                 R a[4];
                 slope<R, D>(Ms, K, d[q + 1], a);  // <a> = dW of this side (Eq. 2.8)
-                mom<R, D>(Ms, a, 0, 0, t);
+                gmul<R, D>(Gs, a, Ms.rho, t);
 #pragma unroll
-                for (int v = 0; v < NV; ++v) dQ[q][v] += Ms.rho * t[v];
+                for (int v = 0; v < NV; ++v) dQ[q][v] += t[v];
                 if (hgks && (q == 0 || (D == 2 && q == 2))) {
                     // half-range (a_n u + a_t v) terms of Eq. 2.6, with and without the flux's u
                     int pu = q == 0 ? 1 : 0, pv = q == 0 ? 0 : 1;
@@ -476,13 +478,17 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         const R Dt = MeshR<R>::dt(g);
         Mom<R, D> M0;
         ok &= maxwellian<R, D>(Q0, gm, K, 0, M0);
+        // <u psi psi> and <v psi psi> of g0 serve every u- and v-weighted moment below
+        Gram<R, D> Gu, Gv;
+        gram<R, D, 1, 0>(M0, Gu);
+        if (D == 2) gram<R, D, 0, 1>(M0, Gv);
         R S1[4], S2[4], z[4], rhs[4], Ab[4], A1t[4], A2t[4] = {0, 0, 0, 0};
         R an[4], at2[4];
         slope<R, D>(M0, K, dQ[0], an);
-        mom<R, D>(M0, an, 1, 0, S1);
+        gmul<R, D>(Gu, an, (R)1, S1);
         if (D == 2) {
             slope<R, D>(M0, K, dQ[2], at2);
-            mom<R, D>(M0, at2, 0, 1, z);
+            gmul<R, D>(Gv, at2, (R)1, z);
 #pragma unroll
             for (int v = 0; v < NV; ++v) S1[v] += z[v];
         }
@@ -492,22 +498,22 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         {
             R ann[4];
             slope<R, D>(M0, K, dQ[1], ann);
-            mom<R, D>(M0, ann, 1, 0, rhs);
+            gmul<R, D>(Gu, ann, (R)1, rhs);
         }
         if (D == 2) {
             R ant[4];
             slope<R, D>(M0, K, dQ[4], ant);
-            mom<R, D>(M0, ant, 0, 1, z);
+            gmul<R, D>(Gv, ant, (R)1, z);
 #pragma unroll
             for (int v = 0; v < NV; ++v) rhs[v] += z[v];
             R s2[4];
-            mom<R, D>(M0, ant, 1, 0, s2);
+            gmul<R, D>(Gu, ant, (R)1, s2);
 #pragma unroll
             for (int v = 0; v < NV; ++v) rhs[v] *= -M0.rho;
             slope<R, D>(M0, K, rhs, A1t);
             R att[4];
             slope<R, D>(M0, K, dQ[3], att);
-            mom<R, D>(M0, att, 0, 1, z);
+            gmul<R, D>(Gv, att, (R)1, z);
 #pragma unroll
             for (int v = 0; v < NV; ++v) rhs[v] = -M0.rho * (s2[v] + z[v]);
             slope<R, D>(M0, K, rhs, A2t);
@@ -516,9 +522,9 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
             for (int v = 0; v < NV; ++v) rhs[v] *= -M0.rho;
             slope<R, D>(M0, K, rhs, A1t);
         }
-        mom<R, D>(M0, A1t, 1, 0, S2);
+        gmul<R, D>(Gu, A1t, (R)1, S2);
         if (D == 2) {
-            mom<R, D>(M0, A2t, 0, 1, z);
+            gmul<R, D>(Gv, A2t, (R)1, z);
 #pragma unroll
             for (int v = 0; v < NV; ++v) S2[v] += z[v];
         }
@@ -527,8 +533,8 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         // flux terms <u> and <A u>; the linear / quadratic fits of Eq. 2.19-2.20
         // and 2.29 reduce to F = <u>, F_t = <A u>, W_t = -S1, W_tt = -S2 at tau = 0
         R F[4], Ft[4], Wt[4], Wtt[4];
-        mom<R, D>(M0, e1, 1, 0, F);
-        mom<R, D>(M0, Ab, 1, 0, Ft);
+        grow0<R, D>(Gu, (R)1, F);
+        gmul<R, D>(Gu, Ab, (R)1, Ft);
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
             F[v] *= M0.rho;
@@ -543,7 +549,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
 #pragma unroll
             for (int v = 0; v < NV; ++v) rhs[v] = -S2[v];
             slope<R, D>(M0, K, rhs, Att);
-            mom<R, D>(M0, Att, 1, 0, T2);
+            gmul<R, D>(Gu, Att, (R)1, T2);
             mom<R, D>(M0, an, 2, 0, T3);
             mom<R, D>(M0, A1t, 2, 0, T4);
             if (D == 2) {
