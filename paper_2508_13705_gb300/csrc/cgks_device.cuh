@@ -389,6 +389,19 @@ __device__ __forceinline__ void recon(const DffR<R>& dff, int oi, int row0, cons
 // compile time, for the 2-D kernels, whose instantiation fixes the order: each
 // linear branch then takes its stencil row from a constant address, so the
 // coefficients enter the FMAs as constant-bank operands instead of loads.
+// The taps of dp = (Qbar_{i-2..i+2} - Qbar_i, h Qx_{i-2..i+2}) that a linear
+// stencil of Sec. 3.2 uses: the own average enters only through the
+// differences (dp[2] = 0) and the own gradient not at all; r5 spans cells
+// i-1..i+1 with the neighbour gradients, r7 cells i-2..i+2 with the gradients
+// of i-1 and i+1, r9 cells i-2..i+2 with the four neighbour gradients.
+__host__ __device__ constexpr bool st_tap(int st, int k)
+{
+    return st == ST_R9 ? (k != 2 && k != 7)
+         : st == ST_R7 ? (k == 0 || k == 1 || k == 3 || k == 4 || k == 6 || k == 8)
+         : st == ST_R5 ? (k == 1 || k == 3 || k == 6 || k == 8)
+         : true;
+}
+
 template <typename R, int NOUT, int OI, int ST, int ROW0>
 __device__ __forceinline__ void recon_lin(const R dp[10], R out[NOUT])
 {
@@ -397,7 +410,8 @@ __device__ __forceinline__ void recon_lin(const R dp[10], R out[NOUT])
     for (int r = 0; r < NOUT; ++r) {
         R s = 0;
 #pragma unroll
-        for (int k = 0; k < 10; ++k) s += T.row[ST][ROW0 + r][k] * dp[k];
+        for (int k = 0; k < 10; ++k)
+            if (st_tap(ST, k)) s += T.row[ST][ROW0 + r][k] * dp[k];
         out[r] = s;
     }
 }

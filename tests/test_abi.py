@@ -79,3 +79,18 @@ def test_host_tables_gauss_rows_reproduce_polynomials(L):
         for l in range(m):
             row = cgks.stencil_row(order, 5, 6 + l)
             assert abs(row @ d - P(x[l])) < 1e-12
+
+
+def test_linear_stencils_use_only_their_taps(L):
+    """The kernels skip, at compile time, the taps a linear stencil of Sec. 3.2
+    does not use (the reconstructing cell's own gradient, and cells outside
+    the stencil); the generated rows must vanish there.  The own-average tap
+    (2) is nonzero in the rows but multiplies Qbar_i - Qbar_i = 0."""
+    used = {3: {1, 3, 6, 8}, 4: {0, 1, 3, 4, 6, 8}, 5: {0, 1, 3, 4, 5, 6, 8, 9}}
+    for order, m in ((5, 2), (7, 3), (9, 4)):
+        for st, taps in used.items():
+            for row in list(range(6)) + list(range(6, 6 + m)):
+                r = cgks.stencil_row(order, st, row)
+                for k in range(10):
+                    if k not in taps and k != 2:
+                        assert r[k] == 0.0, (order, st, row, k)
