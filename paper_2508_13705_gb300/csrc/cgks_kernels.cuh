@@ -143,9 +143,18 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
                     swt[v][q] = lcell<2, M, R>(g, S, dir, 2, v, 0, a, b + q - 2);
                 }
         }
+        // face sigma of the tangential stencil: a direct walk for interior cells
         double s6[6];
+        if (inner) {
+            const double* sp = dir == 0 ? g.sig_y + (long long)(b - 2) * g.nx + a
+                                        : g.sig_x + (long long)a * (g.nx + 1) + (b - 2);
+            const long long ss = dir == 0 ? g.nx : 1;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) s6[q] = lsigT(g, g.sig_x, g.sig_y, dir, a, b - 2 + q);
+            for (int q = 0; q < 6; ++q) s6[q] = sp[q * ss];
+        } else {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) s6[q] = lsigT(g, g.sig_x, g.sig_y, dir, a, b - 2 + q);
+        }
         DffR<R> dff = dff_r<R>(dff_select(g.order, s6, g.thr));
         R ht = (R)(dir == 0 ? g.dy : g.dx);
         long long cidx = cell_idx(dir, na, nb, a, b);
@@ -156,8 +165,16 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         // normal-direction DFF of this cell, reused by every Gauss line in k_normal
         if (a >= -1 && a <= na) {
             double n6[6];
+            if (a >= 2 && a + 3 <= na && b >= 0 && b < nb) {
+                const double* sp = dir == 0 ? g.sig_x + (long long)b * (g.nx + 1) + (a - 2)
+                                            : g.sig_y + (long long)(a - 2) * g.nx + b;
+                const long long ss = dir == 0 ? 1 : g.nx;
 #pragma unroll
-            for (int q = 0; q < 6; ++q) n6[q] = lsigN<2>(g, g.sig_x, g.sig_y, dir, a - 2 + q, b);
+                for (int q = 0; q < 6; ++q) n6[q] = sp[q * ss];
+            } else {
+#pragma unroll
+                for (int q = 0; q < 6; ++q) n6[q] = lsigN<2>(g, g.sig_x, g.sig_y, dir, a - 2 + q, b);
+            }
             R pk[4];
             dff_pack<R>(dff_r<R>(dff_select(g.order, n6, g.thr)), pk);
             st4((R*)g.DN[dir] + cidx * 4, pk);
