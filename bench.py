@@ -31,22 +31,25 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 nominal FP64 rate (non-tensor), profiling re
 HBM_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 # Per cell, per launch of each kernel of a stage (2-D, order 9, tau = 0): the
-# FP operations in the bulk precision (FADD + FMUL + 2 FFMA, or the FP64
-# counterparts in the plain form), the FP64 operations of the FP32-bulk form,
-# and the DRAM bytes read + written.  Counted by ncu (one launch each,
-# --clock-control none) on the 1024^2 vortex; every kernel does the same work
-# per cell at any mesh size (one thread per cell line or face point), so a
-# launch on n^2 cells processes n^2 times these.  The flux kernel's operations
-# per face Gauss point are these over 2 m (n + 1) / n points per cell.
+# FP operations executed in the bulk precision (FADD + FMUL + 2 FFMA, or the
+# FP64 counterparts in the plain form), the FP64 operations of the FP32-bulk
+# form, and the DRAM bytes read + written.  These are the operations the
+# kernels execute, not a count of the method's textbook form: algebra that
+# removes work (Gram-matrix moments, skipped zero taps) lowers them.  Counted
+# by ncu (one launch each, --clock-control none) on the 1024^2 vortex; every
+# kernel does the same work per cell at any mesh size (one thread per cell line
+# or face point), so a launch on n^2 cells processes n^2 times these.  The
+# flux kernel's operations per face Gauss point are these over 2 m (n + 1) / n
+# points per cell.
 KERNEL_COUNTS = {
-    ("fp32", 9): {"s1_lines": (757.9, 24.1, 213.3), "s1_normal": (4473.4, 0.0, 1159.9),
-                  "s1_flux": (24593.9, 0.0, 1319.5), "s1_update": (384.0, 42.0, 969.7),
-                  "s2_lines": (757.9, 24.1, 214.0), "s2_normal": (4473.4, 0.0, 1164.1),
-                  "s2_flux": (23623.0, 0.0, 1019.8), "s2_update": (256.0, 16.0, 892.1)},
-    ("fp64", 9): {"s1_lines": (782.0, 782.0, 449.6), "s1_normal": (4513.5, 4513.5, 2074.3),
-                  "s1_flux": (26874.3, 26874.3, 2789.1), "s1_update": (426.0, 426.0, 1752.9),
-                  "s2_lines": (782.0, 782.0, 449.7), "s2_normal": (4513.5, 4513.5, 2073.5),
-                  "s2_flux": (25617.0, 25617.0, 2253.7), "s2_update": (272.0, 272.0, 1688.1)},
+    ("fp32", 9): {"s1_lines": (612.8, 24.1, 213.9), "s1_normal": (3638.2, 0.0, 1008.4),
+                  "s1_flux": (19501.0, 0.0, 1319.8), "s1_update": (384.0, 42.0, 930.4),
+                  "s2_lines": (612.8, 24.1, 214.5), "s2_normal": (3638.2, 0.0, 1007.8),
+                  "s2_flux": (18554.1, 0.0, 1015.9), "s2_update": (256.0, 16.0, 625.6)},
+    ("fp64", 9): {"s1_lines": (636.9, 636.9, 445.3), "s1_normal": (3678.3, 3678.3, 2072.2),
+                  "s1_flux": (21813.4, 21813.4, 2725.1), "s1_update": (426.0, 426.0, 1751.5),
+                  "s2_lines": (636.9, 636.9, 444.7), "s2_normal": (3678.3, 3678.3, 2071.1),
+                  "s2_flux": (20564.1, 20564.1, 2162.6), "s2_update": (272.0, 272.0, 1158.1)},
 }
 
 
@@ -271,6 +274,7 @@ def main():
         the headline entry is the kernel with the largest share of the step."""
         counts = KERNEL_COUNTS.get((precision, order), {})
         peak = gpu_peak_tflops(precision, sm_count, mhz)
+        hbm = peaks().get("hbm_gbs")
         total = sum(x[1] for x in prof)
         kms = {("s%d_" % (k // 10) if k >= 10 else "") + names_k[k % 10]: v for k, v in prof}
         per = {}
@@ -279,8 +283,9 @@ def main():
                 continue
             fl, _, by = counts[name]
             ach = fl * cells / (ms / 1e3) / 1e12
+            gbs = by * cells / (ms / 1e3) / 1e9
             per[name] = {"ms": round(ms, 4), "achieved_tflops": round(ach, 3), "frac": round(ach / peak, 4),
-                         "dram_gbs": round(by * cells / (ms / 1e3) / 1e9, 1)}
+                         "dram_gbs": round(gbs, 1), "dram_frac": round(gbs / hbm, 4) if hbm else None}
         top = max(per, key=lambda k: per[k]["ms"]) if per else None
         fl, _, by = counts[top] if top else (None, None, None)
         ach = per[top]["achieved_tflops"] if top else None
