@@ -61,12 +61,19 @@ int load_tables()
     return CGKS_OK;
 }
 
-Kfns pick_kfns(int dim, int order, int prec)
+Kfns pick_kfns(int dim, int order, int prec, int tau_mode)
 {
     int M = (order - 1) / 2;
-    if (dim == 1) return prec == CGKS_FP64 ? kfns_1_1_d() : kfns_1_1_f();
-    if (prec == CGKS_FP64) return M == 2 ? kfns_2_2_d() : (M == 3 ? kfns_2_3_d() : kfns_2_4_d());
-    return M == 2 ? kfns_2_2_f() : (M == 3 ? kfns_2_3_f() : kfns_2_4_f());
+    Kfns k;
+    if (dim == 1) k = prec == CGKS_FP64 ? kfns_1_1_d() : kfns_1_1_f();
+    else if (prec == CGKS_FP64) k = M == 2 ? kfns_2_2_d() : (M == 3 ? kfns_2_3_d() : kfns_2_4_d());
+    else k = M == 2 ? kfns_2_2_f() : (M == 3 ? kfns_2_3_f() : kfns_2_4_f());
+    // the flux instances of the mesh's collision-time mode
+    if (tau_mode == CGKS_TAU_HGKS)
+        for (int c = 0; c < 2; ++c) { k.flux1v[c] = k.flux1h[c]; k.flux2v[c] = k.flux2h[c]; }
+    k.flux1 = k.flux1v[0];
+    k.flux2 = k.flux2v[0];
+    return k;
 }
 
 enum { W_LINES = 0, W_NORMAL, W_FLUX, W_CELLS, W_SIGINIT, W_COUNT };
@@ -269,7 +276,7 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return CGKS_ECUDA; }
         b->own_stream = true;
     }
-    b->k = pick_kfns(p->dim, p->order, p->precision);
+    b->k = pick_kfns(p->dim, p->order, p->precision, p->tau_mode);
     std::vector<Layout> L(n);
     size_t total = 0;
     std::vector<size_t> base(n);
@@ -1005,7 +1012,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     if (sigma_in && sigma_in != sigma_out)
         CK(cudaMemcpyAsync(sigma_out, sigma_in, (size_t)(nx + 1) * 8, cudaMemcpyDeviceToDevice, st));
     if (dt > 0.0) CK(cudaMemcpyAsync(g.dt + 0, &dt, 8, cudaMemcpyHostToDevice, st));
-    Kfns k = pick_kfns(1, p->order, p->precision);
+    Kfns k = pick_kfns(1, p->order, p->precision, p->tau_mode);
     int nsm = 1;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     auto go = [&](const void* fn, int kind, int stage, bool has_stage, int threads) -> int {

@@ -349,8 +349,10 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
 // Eq. 2.6 as soon as they are formed, so only one side is live at a time.
 // CAP = 1 asks for at least 4 resident blocks of 128 threads (<= 128 registers,
 // spilling the rest); CAP = 0 for 3 in FP32 (<= 170 registers, no spills) and
-// 1 in FP64.  The autotuner times both variants.
-template <int D, int M, typename R, int STAGE, int CAP>
+// 1 in FP64.  The autotuner times both variants.  HG = 1 compiles the
+// collision-time terms (tau > 0); the tau = 0 instance leaves them out and
+// carries fewer live values.
+template <int D, int M, typename R, int STAGE, int CAP, int HG>
 __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flux(Work w)
 {
     constexpr int NV = D + 2;
@@ -386,7 +388,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         else { unsigned d = nb, q = r / d; b = (int)(r - q * d); f = (int)q; }
         const R* FR = (const R*)g.FR[dir];
         const R gm = MeshR<R>::gamma(g), K = MeshR<R>::K(g);
-        const bool hgks = g.tau_mode == 1;
+        constexpr bool hgks = HG != 0;  // the collision-time terms of Eq. 2.6 (tau > 0)
         R e1[4] = {1, 0, 0, 0};
         R Q0[4] = {0, 0, 0, 0};
         R dQ[ND][4];

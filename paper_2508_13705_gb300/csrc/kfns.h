@@ -10,7 +10,8 @@ struct Kfns {
     KStage lines, normal;
     KOne flux1, flux2, upd1, upd2, cfl, siginit, check;
     KStage convert;  // FP32-bulk state copies (to_float = 1: FP64 -> float planes)
-    KOne flux1v[2], flux2v[2];  // flux variants: [0] uncapped, [1] register-capped
+    KOne flux1v[2], flux2v[2];  // flux variants: [0] uncapped, [1] register-capped (tau = 0)
+    KOne flux1h[2], flux2h[2];  // the same with the collision-time terms (tau > 0)
     int (*upload)(const CgksTables* t3, const TabF* f3);  // constant tables of this unit
 };
 Kfns kfns_1_1_d();

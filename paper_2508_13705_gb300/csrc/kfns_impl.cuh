@@ -19,10 +19,14 @@ Kfns make_kfns()
     Kfns k;
     k.lines = D == 2 ? (KStage)k_lines<M, R> : nullptr;
     k.normal = k_normal<D, M, R>;
-    k.flux1v[0] = k_flux<D, M, R, 1, 0>;
-    k.flux2v[0] = k_flux<D, M, R, 2, 0>;
-    k.flux1v[1] = k_flux<D, M, R, 1, 1>;
-    k.flux2v[1] = k_flux<D, M, R, 2, 1>;
+    k.flux1v[0] = k_flux<D, M, R, 1, 0, 0>;
+    k.flux2v[0] = k_flux<D, M, R, 2, 0, 0>;
+    k.flux1v[1] = k_flux<D, M, R, 1, 1, 0>;
+    k.flux2v[1] = k_flux<D, M, R, 2, 1, 0>;
+    k.flux1h[0] = k_flux<D, M, R, 1, 0, 1>;
+    k.flux2h[0] = k_flux<D, M, R, 2, 0, 1>;
+    k.flux1h[1] = k_flux<D, M, R, 1, 1, 1>;
+    k.flux2h[1] = k_flux<D, M, R, 2, 1, 1>;
     k.flux1 = k.flux1v[0];
     k.flux2 = k.flux2v[0];
     if (D == 2) { k.upd1 = (KOne)k_update2<M, R, 1>; k.upd2 = (KOne)k_update2<M, R, 2>; }
