@@ -42,14 +42,14 @@ HBM_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # flux kernel's operations per face Gauss point are these over 2 m (n + 1) / n
 # points per cell.
 KERNEL_COUNTS = {
-    ("fp32", 9): {"s1_lines": (612.8, 24.1, 213.9), "s1_normal": (3638.2, 0.0, 1008.4),
-                  "s1_flux": (19501.0, 0.0, 1319.8), "s1_update": (384.0, 42.0, 930.4),
-                  "s2_lines": (612.8, 24.1, 214.5), "s2_normal": (3638.2, 0.0, 1007.8),
-                  "s2_flux": (18554.1, 0.0, 1015.9), "s2_update": (256.0, 16.0, 625.6)},
-    ("fp64", 9): {"s1_lines": (636.9, 636.9, 445.3), "s1_normal": (3678.3, 3678.3, 2072.2),
-                  "s1_flux": (21813.4, 21813.4, 2725.1), "s1_update": (426.0, 426.0, 1751.5),
-                  "s2_lines": (636.9, 636.9, 444.7), "s2_normal": (3678.3, 3678.3, 2071.1),
-                  "s2_flux": (20564.1, 20564.1, 2162.6), "s2_update": (272.0, 272.0, 1158.1)},
+    ("fp32", 9): {"s1_lines": (612.8, 24.1, 215.9), "s1_normal": (3638.2, 0.0, 1009.2),
+                  "s1_flux": (19284.8, 0.0, 1319.5), "s1_update": (384.0, 42.0, 930.6),
+                  "s2_lines": (612.8, 24.1, 216.4), "s2_normal": (3638.2, 0.0, 1008.4),
+                  "s2_flux": (18329.9, 0.0, 1015.8), "s2_update": (256.0, 16.0, 625.7)},
+    ("fp64", 9): {"s1_lines": (636.9, 636.9, 447.1), "s1_normal": (3678.3, 3678.3, 2072.2),
+                  "s1_flux": (21492.8, 21492.8, 2761.3), "s1_update": (426.0, 426.0, 1751.8),
+                  "s2_lines": (636.9, 636.9, 447.2), "s2_normal": (3678.3, 3678.3, 2072.9),
+                  "s2_flux": (20275.8, 20275.8, 2192.0), "s2_update": (272.0, 272.0, 1158.0)},
 }
 
 
@@ -64,7 +64,37 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--profile-case", choices=["fp32", "fp64"], default=None,
+                    help="run one warm-up step and one step kernel by kernel on the --n vortex in the "
+                         "given form, then exit (the small case the ncu captures use)")
     return ap.parse_args()
+
+
+def profile_case(a):
+    """Autotune, one warm-up S2O4 step, then one step launched kernel by kernel
+    (no graph) inside the NVTX range `profiled`, on the n x n order-`order`
+    vortex: the bench's launch shapes in a short launch sequence for ncu."""
+    import torch
+
+    from paper_2508_13705_gb300 import build, cgks
+    build.build()
+    st = vortex_inputs(a.n, a.order)
+    prec = cgks.FP32_BULK if a.profile_case == "fp32" else cgks.FP64
+    s = cgks.Solver(2, a.order, a.n, a.n, extent=(0.0, 10.0, 0.0, 10.0), precision=prec)
+    s.set_state(*st)
+    tuned = s.autotune()
+    s.advance(1, 0.0)
+    s.sync()
+    dt = s.compute_dt()
+    torch.cuda.nvtx.range_push("profiled")
+    ms = s.profile_step(dt)
+    s.sync()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile_case": a.profile_case, "n": a.n, "order": a.order,
+                      "autotuned_threads": tuned, "kernels_ms": ms}))
+    s.sync()
+    s.close()
+    torch.cuda.synchronize()
 
 
 def dist_setup(n):
@@ -185,6 +215,8 @@ def main():
     a = parse()
     if a.impl == "reference":
         return reference_arm(a)
+    if a.profile_case:
+        return profile_case(a)
     import torch
 
     from paper_2508_13705_gb300 import build, cgks
