@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-config3", action="store_true")
     ap.add_argument("--profile-case", choices=["fp32", "fp64"], default=None,
                     help="run one warm-up step and one step kernel by kernel on the --n vortex in the "
                          "given form, then exit (the small case the ncu captures use)")
@@ -359,6 +360,8 @@ def main():
         line["accuracy"] = accuracy(torch, cgks, order, stream)
     if rank == 0 and not a.no_batch:
         line["batch"] = batch_bench(torch, cgks, stream)
+    if rank == 0 and not a.no_config3:
+        line["config3"] = config3_bench(torch, cgks, stream)
     if rank == 0 and not a.no_cpu:
         rate, cores, el = cpu_oracle_rate(order, 128, 2)
         line["cpu_baseline"] = {"value": round(rate, 5), "unit": "Mcell-stage/s", "cores": cores, "kind": "oracle",
@@ -460,6 +463,71 @@ def batch_bench(torch, cgks, stream, count=256, order=7, steps=10):
             "fp64_one_at_a_time": {"value": round(cells * 2 * k64 / (ms64 / 1e3) / 1e6, 3),
                                    "unit": "Mcell-stage/s", "steps": k64},
             "input_gen_s": round(t_in, 1)}
+
+
+# The paper's CPU time (s) of the reconstruction alone over 20 steps of
+# Configuration 3, one Xeon Gold 6133 core (the CPU-time table of Sec. 4),
+# for orders 5, 7, 9 by mesh side.  Context only: other hardware, and a
+# part of the step.
+PAPER_RECON_CPU_S = {100: (0.913, 1.382, 1.942), 200: (5.244, 6.048, 7.685),
+                     400: (15.764, 28.722, 30.228), 800: (63.766, 126.264, 119.484)}
+
+
+def config3_bench(torch, cgks, stream, full_order=9):
+    """Sec. 4.7 Configuration 3, the paper's timing workload: (1) 20 whole S2O4
+    steps (CFL step on the device, HGKS tau, transmissive) at the four meshes
+    of the paper's CPU-time table, FP64 and FP32 bulk, beside the paper's
+    reconstruction-only CPU times; (2) the full run at 500^2 to t = 0.6."""
+    from paper_2508_13705_gb300 import inputs
+    states, split = inputs.CONFIG3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def solver(n, order, prec):
+        s = cgks.Solver(2, order, n, n, extent=(0.0, 1.0, 0.0, 1.0), precision=prec, tau_mode=cgks.TAU_HGKS,
+                        bc=(1, 1, 1, 1), stream=stream.cuda_stream)
+        s.set_state(*inputs.quadrants_2d(n, order, states=states, split=split))
+        s.autotune()
+        return s
+
+    table = []
+    for n, paper in PAPER_RECON_CPU_S.items():
+        row = {"mesh": n, "paper_recon_cpu_s_orders_5_7_9": list(paper)}
+        for prec, key in ((cgks.FP64, "fp64"), (cgks.FP32_BULK, "fp32")):
+            ms = []
+            for order in (5, 7, 9):
+                s = solver(n, order, prec)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                s.advance(20, 0.0)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(round(e0.elapsed_time(e1), 3))
+                _, rc, _ = s.sync(raise_on_error=False)
+                s.close()
+                if rc:
+                    ms[-1] = None
+            row[key + "_20_steps_ms_orders_5_7_9"] = ms
+        table.append(row)
+    full = {}
+    for prec, key in ((cgks.FP32_BULK, "fp32"), (cgks.FP64, "fp64")):
+        s = solver(500, full_order, prec)
+        t, steps = 0.0, 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        while t < 0.6 - 1e-14:
+            dt = min(s.compute_dt(), 0.6 - t)
+            s.step(dt)
+            t += dt
+            steps += 1
+        _, rc, _ = s.sync(raise_on_error=False)
+        wall = time.perf_counter() - t0
+        s.close()
+        full[key] = {"steps": steps, "wall_s": round(wall, 3), "status": rc,
+                     "Mcell_stage_per_s": round(500 * 500 * 2 * steps / wall / 1e6, 3)}
+    return {"workload": "2-D Riemann Configuration 3 (Sec. 4.7), transmissive, HGKS tau, CFL 0.5",
+            "twenty_steps": table,
+            "full_run_500_t0.6_order%d" % full_order: full,
+            "note": "paper times: reconstruction only, one CPU core; GPU times: whole steps incl. CFL"}
 
 
 def reference_arm(a):

@@ -211,9 +211,19 @@ def quadrant_states(seed=0, gamma=1.4):
             return s
 
 
-def quadrants_2d(n, order, seed=0, gamma=1.4, split=(0.5, 0.5)):
-    """Four-quadrant Riemann problem on [0,1]^2 (split on cell faces); zero slopes."""
-    s = quadrant_states(seed, gamma)
+# Sec. 4.7: the four-quadrant states (rho, u, v, p) of Configurations 2 and 3
+# for quadrants (SW, SE, NE, NW) and the split point.
+CONFIG2 = (np.array([[1.0, -0.7259, -0.7259, 1.0], [0.5197, 0.0, -0.7259, 0.4], [1.0, 0.0, 0.0, 1.0],
+                     [0.5197, -0.7259, 0.0, 0.4]]), (0.5, 0.5))
+CONFIG3 = (np.array([[0.138, 1.206, 1.206, 0.029], [0.5323, 0.0, 1.206, 0.3], [1.5, 0.0, 0.0, 1.5],
+                     [0.5323, 1.206, 0.0, 0.3]]), (0.7, 0.7))
+
+
+def quadrants_2d(n, order, seed=0, gamma=1.4, split=(0.5, 0.5), states=None):
+    """Four-quadrant Riemann problem on [0,1]^2 (split on cell faces); zero
+    slopes.  ``states`` (SW, SE, NE, NW rows of rho, u, v, p) defaults to the
+    seeded draw of quadrant_states(seed)."""
+    s = quadrant_states(seed, gamma) if states is None else np.asarray(states, dtype=float)
     h = 1.0 / n
     xc = (np.arange(n) + 0.5) * h
     east = (xc >= split[0])[None, :]

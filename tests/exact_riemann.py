@@ -4,6 +4,8 @@ Textbook construction: the star-region pressure p* solves
 f_L(p*) + f_R(p*) + (u_R - u_L) = 0, where f_K is the shock (Rankine-Hugoniot)
 branch for p* > p_K and the rarefaction (isentropic) branch otherwise; it is
 found by Newton iteration.  The self-similar solution is then sampled at x/t.
+When 2 (a_L + a_R) / (gamma - 1) <= u_R - u_L no p* > 0 exists: the two
+rarefactions separate and leave a vacuum between their tails.
 """
 import numpy as np
 
@@ -38,12 +40,57 @@ def star_state(left, right, gamma=1.4):
     return p, u
 
 
+def _fan_left(left, s, g):
+    rl, ul, pl = left
+    al = np.sqrt(g * pl / rl)
+    c = 2 / (g + 1) + (g - 1) / ((g + 1) * al) * (ul - s)
+    return (rl * c ** (2 / (g - 1)), 2 / (g + 1) * (al + (g - 1) / 2 * ul + s), pl * c ** (2 * g / (g - 1)))
+
+
+def _fan_right(right, s, g):
+    rr, ur, pr = right
+    ar = np.sqrt(g * pr / rr)
+    c = 2 / (g + 1) - (g - 1) / ((g + 1) * ar) * (ur - s)
+    return (rr * c ** (2 / (g - 1)), 2 / (g + 1) * (-ar + (g - 1) / 2 * ur + s), pr * c ** (2 * g / (g - 1)))
+
+
+def generates_vacuum(left, right, gamma=1.4):
+    """Pressure-positivity condition fails: the two rarefactions separate."""
+    al, ar = np.sqrt(gamma * left[2] / left[0]), np.sqrt(gamma * right[2] / right[0])
+    return 2 * (al + ar) / (gamma - 1) <= right[1] - left[1]
+
+
+def _sample_vacuum(left, right, xi, g):
+    """Two rarefactions whose tails, u_L + 2a_L/(g-1) and u_R - 2a_R/(g-1),
+    bound a vacuum (rho = p = 0)."""
+    rl, ul, pl = left
+    rr, ur, pr = right
+    al, ar = np.sqrt(g * pl / rl), np.sqrt(g * pr / rr)
+    sl, sr = ul + 2 * al / (g - 1), ur - 2 * ar / (g - 1)
+    out = np.zeros((3, len(xi)))
+    for n, s in enumerate(xi):
+        if s <= ul - al:
+            out[:, n] = left
+        elif s < sl:
+            out[:, n] = _fan_left(left, s, g)
+        elif s <= sr:
+            out[:, n] = (0.0, s, 0.0)
+        elif s < ur + ar:
+            out[:, n] = _fan_right(right, s, g)
+        else:
+            out[:, n] = right
+    return out
+
+
 def sample(left, right, xi, gamma=1.4):
     """(rho, u, p) at similarity coordinates xi = (x - x0) / t (array)."""
     rl, ul, pl = left
     rr, ur, pr = right
-    ps, us = star_state(left, right, gamma)
     g = gamma
+    xi = np.atleast_1d(np.asarray(xi, dtype=float))
+    if generates_vacuum(left, right, g):
+        return _sample_vacuum(left, right, xi, g)
+    ps, us = star_state(left, right, gamma)
     al, ar = np.sqrt(g * pl / rl), np.sqrt(g * pr / rr)
     out = np.zeros((3, len(xi)))
     for n, s in enumerate(xi):
@@ -62,9 +109,7 @@ def sample(left, right, xi, gamma=1.4):
                 elif s >= us - ast:
                     out[:, n] = (rl * (ps / pl) ** (1 / g), us, ps)
                 else:
-                    c = 2 / (g + 1) + (g - 1) / ((g + 1) * al) * (ul - s)
-                    out[:, n] = (rl * c ** (2 / (g - 1)), 2 / (g + 1) * (al + (g - 1) / 2 * ul + s),
-                                 pl * c ** (2 * g / (g - 1)))
+                    out[:, n] = _fan_left(left, s, g)
         else:  # right of contact
             if ps > pr:
                 sr = ur + ar * np.sqrt((g + 1) / (2 * g) * ps / pr + (g - 1) / (2 * g))
@@ -80,9 +125,7 @@ def sample(left, right, xi, gamma=1.4):
                 elif s <= us + ast:
                     out[:, n] = (rr * (ps / pr) ** (1 / g), us, ps)
                 else:
-                    c = 2 / (g + 1) - (g - 1) / ((g + 1) * ar) * (ur - s)
-                    out[:, n] = (rr * c ** (2 / (g - 1)), 2 / (g + 1) * (-ar + (g - 1) / 2 * ur + s),
-                                 pr * c ** (2 * g / (g - 1)))
+                    out[:, n] = _fan_right(right, s, g)
     return out
 
 

@@ -40,16 +40,18 @@ def slope_floor(orc):
     return 64 * np.finfo(float).eps * np.abs(orc.W).max() / h
 
 
-def compare(gpu, orc, fields, tol=TOL, what=""):
+def compare(gpu, orc, fields, tol=TOL, what="", sigma_floor=1e-14):
     """Cell averages: relative L1 <= tol.  Slope fields: relative L1 <= tol
     on top of the rounding floor of slope_floor() per value.  sigma (Eq. 3.2)
     of smooth data is a difference of nearly equal pressures (~1e-11), so it
-    is compared elementwise with an absolute floor of 1e-14."""
+    is compared elementwise with an absolute floor (1e-14 by default; flows
+    at Mach number Ma carry (Delta Ma)^2 terms whose rounding scales with
+    Ma^2, and pass a floor scaled by it)."""
     o = orc.get_state()
     for f in fields:
         if f.startswith("sigma"):
             err = np.abs(gpu[f] - o[f]) - tol * np.abs(o[f])
-            assert err.max() <= 1e-14, "%s %s: max excess %.3e" % (what, f, err.max())
+            assert err.max() <= sigma_floor, "%s %s: max excess %.3e" % (what, f, err.max())
         elif f == "W":
             e = rel_l1(gpu[f], o[f])
             assert e <= tol, "%s %s: rel L1 %.3e" % (what, f, e)
