@@ -55,10 +55,19 @@ extern "C" {
 /* collision time (Sec. 4) */
 #define CGKS_TAU_ZERO 0      /* tau = 0 (smooth inviscid tests, Sec. 4.6) */
 #define CGKS_TAU_HGKS 1      /* tau = c1 dt + c2 |pl - pr| / (pl + pr) dt */
+#define CGKS_TAU_NS 2        /* viscous flow (Sec. 4): tau = mu / p + c2 |pl - pr| / (pl + pr) dt,
+                                p the pressure of the equilibrium state at the face point;
+                                the time step adds the limit dx^2 / (4 nu), nu = mu / rho */
 /* boundary conditions, per side: bc[0..3] = x-low, x-high, y-low, y-high */
 #define CGKS_BC_PERIODIC 0
 #define CGKS_BC_TRANSMISSIVE 1  /* ghost = nearest interior cell, normal slopes zero */
 #define CGKS_BC_FIXED 2         /* 1-D only: ghost cells fixed by cgks_set_ghost */
+#define CGKS_BC_REFLECTIVE 3    /* slip wall (Sec. 4.4, and the symmetry plane of Sec. 4.9):
+                                   ghost cell k = mirror image of interior cell k (the
+                                   cell and line averages and slopes reflected, the
+                                   normal momentum reversed); ghost faces mirror sigma */
+#define CGKS_BC_NOSLIP 4        /* adiabatic no-slip wall (Sec. 4.9): the same mirror with
+                                   both momentum components reversed */
 
 typedef struct {
     int dim;            /* 1 or 2 */
@@ -74,6 +83,7 @@ typedef struct {
     double weno_eps;    /* epsilon of the WENO-Z weights, Eq. 3.14 (1e-8) */
     double tau_c1;      /* c1 of the HGKS collision time (0.05) */
     double tau_c2;      /* c2 of the HGKS collision time (1.0) */
+    double mu;          /* dynamic viscosity of CGKS_TAU_NS (constant), >= 0 */
 } cgks_params;
 
 typedef struct cgks_solver cgks_solver;
@@ -90,7 +100,7 @@ typedef struct {
 } cgks_stats;
 
 /* Fill *p with the paper's defaults for (dim, order): gamma 1.4, CFL 0.5,
- * sigma_thres 1, gamma_hi 0.85, gamma_lo 0.6, eps 1e-8, c1 0.05, c2 1,
+ * sigma_thres 1, gamma_hi 0.85, gamma_lo 0.6, eps 1e-8, c1 0.05, c2 1, mu 0,
  * FP64, tau = 0, periodic.  Returns CGKS_EINVAL for a NULL p. */
 int cgks_default_params(cgks_params* p, int dim, int order);
 

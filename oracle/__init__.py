@@ -37,8 +37,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 
-BC_PERIODIC, BC_TRANSMISSIVE, BC_FIXED = 0, 1, 2
-TAU_ZERO, TAU_HGKS = 0, 1
+BC_PERIODIC, BC_TRANSMISSIVE, BC_FIXED, BC_REFLECTIVE, BC_NOSLIP = 0, 1, 2, 3, 4
+TAU_ZERO, TAU_HGKS, TAU_NS = 0, 1, 2
 
 
 def build(force=False):
@@ -62,7 +62,7 @@ class OParams(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("sigma_thres", ctypes.c_double), ("gamma_hi", ctypes.c_double),
                 ("gamma_lo", ctypes.c_double), ("weno_eps", ctypes.c_double),
-                ("c1", ctypes.c_double), ("c2", ctypes.c_double)]
+                ("c1", ctypes.c_double), ("c2", ctypes.c_double), ("mu", ctypes.c_double)]
 
 
 _lib = None
@@ -107,7 +107,7 @@ class Oracle:
 
     def __init__(self, dim, order, nx, ny=1, extent=(0.0, 1.0, 0.0, 1.0), gamma=1.4, cfl=0.5,
                  tau_mode=TAU_ZERO, bc=(BC_PERIODIC,) * 4, sigma_thres=1.0, gamma_hi=0.85,
-                 gamma_lo=0.6, weno_eps=1e-8, c1=0.05, c2=1.0, step3=0):
+                 gamma_lo=0.6, weno_eps=1e-8, c1=0.05, c2=1.0, step3=0, mu=0.0):
         assert dim in (1, 2) and order in (5, 7, 9)
         self.dim, self.order, self.nx, self.ny = dim, order, nx, (ny if dim == 2 else 1)
         self.nv = dim + 2
@@ -127,6 +127,8 @@ class Oracle:
         P.dx, P.dy, P.gamma = self.dx, self.dy, gamma
         P.sigma_thres, P.gamma_hi, P.gamma_lo = sigma_thres, gamma_hi, gamma_lo
         P.weno_eps, P.c1, P.c2 = weno_eps, c1, c2
+        P.mu = mu
+        self.mu, self.tau_mode = mu, tau_mode
         self.P = P
         tabs = coeffs.poly_tables()
         self.T = np.ascontiguousarray(np.stack([tabs[k] for k in ("S0", "S1", "S2", "r5", "r7", "r9")]))
@@ -165,16 +167,30 @@ class Oracle:
         n = W.shape[2 - axis]
         lo_bc, hi_bc = self.bc[2 * axis], self.bc[2 * axis + 1]
         take = lambda k: np.take(W, [k], axis=2 - axis)
+
+        def mirror(q, bc):
+            # the wall's ghost cell: the adjacent cell with the normal momentum
+            # (slip) or every momentum component (no-slip) reversed
+            q = q.copy()
+            for v in range(1, self.nv - 1):
+                if v == 1 + axis or bc == BC_NOSLIP:
+                    q[v] = -q[v]
+            return q
+
         if lo_bc == BC_PERIODIC:
             lo = take(n - 1)
         elif lo_bc == BC_FIXED:
             lo = self.ghost[0, 0, 0].reshape(-1, 1, 1)
+        elif lo_bc in (BC_REFLECTIVE, BC_NOSLIP):
+            lo = mirror(take(0), lo_bc)
         else:
             lo = take(0)
         if hi_bc == BC_PERIODIC:
             hi = take(0)
         elif hi_bc == BC_FIXED:
             hi = self.ghost[1, 0, 0].reshape(-1, 1, 1)
+        elif hi_bc in (BC_REFLECTIVE, BC_NOSLIP):
+            hi = mirror(take(n - 1), hi_bc)
         else:
             hi = take(n - 1)
         ext = np.concatenate([lo, W, hi], axis=2 - axis)
@@ -215,7 +231,8 @@ class Oracle:
 
     # ---------------------------------------------------------------- physics
     def compute_dt(self):
-        """CFL rule (Sec. 4): dt = C * min over cells of h / (|U| + a_s)."""
+        """CFL rule (Sec. 4): dt = C * min over cells of h / (|U| + a_s), and for
+        viscous flow also of h^2 / (4 nu) with nu = mu / rho."""
         W, g = self.W, self.gamma
         rho = W[0]
         u = W[1] / rho
@@ -223,7 +240,10 @@ class Oracle:
         p = (g - 1.0) * (W[self.dim + 1] - 0.5 * rho * (u * u + v * v))
         a = np.sqrt(g * p / rho)
         h = min(self.dx, self.dy) if self.dim == 2 else self.dx
-        return float(self.cfl * np.min(h / (np.sqrt(u * u + v * v) + a)))
+        lim = h / (np.sqrt(u * u + v * v) + a)
+        if self.tau_mode == TAU_NS and self.mu > 0:
+            lim = np.minimum(lim, h * h / (4.0 * self.mu / rho))
+        return float(self.cfl * np.min(lim))
 
     def faces(self, dt, state=None):
         """One stage's face evaluation.  Returns (out_x, sig_x[, out_y, sig_y])."""

@@ -22,7 +22,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_FIXED = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_FIXED = 2, BC_REFLECTIVE = 3, BC_NOSLIP = 4 };
 enum { K_W = 0, K_WX = 1, K_WY = 2, K_WXL = 3, K_WYL = 4 };
 enum { ST_S0 = 0, ST_S1 = 1, ST_S2 = 2, ST_R5 = 3, ST_R7 = 4, ST_R9 = 5 };
 /* flag bits */
@@ -33,13 +33,14 @@ enum { FL_NONPHYS = 1 };
 typedef struct {
     int dim, order, m, nx, ny;
     int bc[4];       /* xlo, xhi, ylo, yhi */
-    int tau_mode;    /* 0: tau = 0, 1: tau = c1 dt + c2 |pl-pr|/(pl+pr) dt */
+    int tau_mode;    /* 0: tau = 0, 1: tau = c1 dt + c2 |pl-pr|/(pl+pr) dt, 2: mu/p0 + c2 |pl-pr|/(pl+pr) dt */
     int step3;       /* 0: Lagrange through 3m face points, 1: 3-point central */
     int flux_tt;     /* 1: keep the t^2/2 a_tt g0 term of Eq. 2.6 in the flux integral */
     int dff_faces;   /* 0: all faces of the stencil's cells, 1: interior faces only */
     int step3_deg;   /* Step 3 fit degree through the 3m points (0: 3m-1, interpolation) */
     double dx, dy, gamma;
     double sigma_thres, gamma_hi, gamma_lo, weno_eps, c1, c2;
+    double mu;       /* dynamic viscosity (tau_mode 2) */
 } OParams;
 
 typedef struct {
@@ -61,10 +62,25 @@ static int imod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
 /* Cell field value with the ghost-cell rule applied direction by direction:
  * periodic wraps; transmissive copies the nearest interior cell and zeroes
  * the slopes normal to that boundary; fixed (1-D) reads the stored ghost. */
+static int is_wall(int bc) { return bc == BC_REFLECTIVE || bc == BC_NOSLIP; }
+
+/* Sign of a mirrored ghost value across a wall whose normal is the x axis
+ * (normal = 0) or the y axis (normal = 1).  Reflection x -> -x maps a field
+ * q to S q(-x), with S reversing the normal momentum (slip wall) or both
+ * momenta (no-slip wall); a derivative along the normal picks up one more
+ * sign, a derivative along the wall none. */
+static double wall_sign(int kind, int v, int normal, int bc, int nv)
+{
+    int rev = (v == 1 + normal) || (bc == BC_NOSLIP && v >= 1 && v <= nv - 2);
+    int dnormal = normal == 0 ? (kind == K_WX || kind == K_WXL) : (kind == K_WY || kind == K_WYL);
+    return (rev ^ dnormal) ? -1.0 : 1.0;
+}
+
 static double cellval(const Ctx *c, int kind, int v, int l, int i, int j)
 {
     const OParams *P = c->P;
     int nx = P->nx, ny = P->ny, zero = 0;
+    double sgn = 1.0;
     if (i < 0 || i >= nx) {
         int side = i < 0 ? 0 : 1;
         int bc = P->bc[side];
@@ -74,6 +90,11 @@ static double cellval(const Ctx *c, int kind, int v, int l, int i, int j)
             int layer = side == 0 ? (-1 - i) : (i - nx);
             int f = kind == K_W ? 0 : 1;
             return c->ghost[((side * 3 + layer) * 2 + f) * 3 + v];
+        } else if (is_wall(bc)) {
+            /* ghost cell -1-k mirrors cell k; lines across x (Wy_line) swap ends */
+            i = i < 0 ? -1 - i : 2 * nx - 1 - i;
+            sgn *= wall_sign(kind, v, 0, bc, c->nv);
+            if (kind == K_WYL) l = P->m - 1 - l;
         } else {
             i = i < 0 ? 0 : nx - 1;
             if (kind == K_WX || kind == K_WXL) zero = 1;
@@ -83,6 +104,10 @@ static double cellval(const Ctx *c, int kind, int v, int l, int i, int j)
         int bc = P->bc[j < 0 ? 2 : 3];
         if (bc == BC_PERIODIC) {
             j = imod(j, ny);
+        } else if (is_wall(bc)) {
+            j = j < 0 ? -1 - j : 2 * ny - 1 - j;
+            sgn *= wall_sign(kind, v, 1, bc, c->nv);
+            if (kind == K_WXL) l = P->m - 1 - l;
         } else {
             j = j < 0 ? 0 : ny - 1;
             if (kind == K_WY || kind == K_WYL) zero = 1;
@@ -91,38 +116,51 @@ static double cellval(const Ctx *c, int kind, int v, int l, int i, int j)
     if (zero) return 0.0;
     size_t plane = (size_t)nx * ny;
     size_t idx = (size_t)j * nx + i;
+    double val;
     switch (kind) {
-    case K_W: return c->W[v * plane + idx];
-    case K_WX: return c->Wx[v * plane + idx];
-    case K_WY: return c->Wy[v * plane + idx];
-    case K_WXL: return c->Wxl[((size_t)l * c->nv + v) * plane + idx];
-    default: return c->Wyl[((size_t)l * c->nv + v) * plane + idx];
+    case K_W: val = c->W[v * plane + idx]; break;
+    case K_WX: val = c->Wx[v * plane + idx]; break;
+    case K_WY: val = c->Wy[v * plane + idx]; break;
+    case K_WXL: val = c->Wxl[((size_t)l * c->nv + v) * plane + idx]; break;
+    default: val = c->Wyl[((size_t)l * c->nv + v) * plane + idx]; break;
     }
+    return sgn * val;
 }
-
-/* sigma of x-face f (face x_{f-1/2}, f in [0,nx]) in row j */
+/* Face sigma beyond a wall mirrors the interior face (face 0 is the wall). */
 static double sigx(const Ctx *c, int f, int j)
 {
     const OParams *P = c->P;
     int nx = P->nx, ny = P->ny;
     if (f < 0 || f > nx) {
-        if (P->bc[f < 0 ? 0 : 1] != BC_PERIODIC) return 0.0;
-        f = imod(f, nx);
+        int bc = P->bc[f < 0 ? 0 : 1];
+        if (bc == BC_PERIODIC) f = imod(f, nx);
+        else if (is_wall(bc)) f = f < 0 ? -f : 2 * nx - f;
+        else return 0.0;
     }
-    if (j < 0 || j >= ny) j = P->bc[j < 0 ? 2 : 3] == BC_PERIODIC ? imod(j, ny) : (j < 0 ? 0 : ny - 1);
+    if (j < 0 || j >= ny) {
+        int bc = P->bc[j < 0 ? 2 : 3];
+        if (bc == BC_PERIODIC) j = imod(j, ny);
+        else if (is_wall(bc)) j = j < 0 ? -1 - j : 2 * ny - 1 - j;
+        else j = j < 0 ? 0 : ny - 1;
+    }
     return c->sx[(size_t)j * (nx + 1) + f];
 }
-
-/* sigma of y-face g (face y_{g-1/2}, g in [0,ny]) in column i */
 static double sigy(const Ctx *c, int i, int g)
 {
     const OParams *P = c->P;
     int nx = P->nx, ny = P->ny;
     if (g < 0 || g > ny) {
-        if (P->bc[g < 0 ? 2 : 3] != BC_PERIODIC) return 0.0;
-        g = imod(g, ny);
+        int bc = P->bc[g < 0 ? 2 : 3];
+        if (bc == BC_PERIODIC) g = imod(g, ny);
+        else if (is_wall(bc)) g = g < 0 ? -g : 2 * ny - g;
+        else return 0.0;
     }
-    if (i < 0 || i >= nx) i = P->bc[i < 0 ? 0 : 1] == BC_PERIODIC ? imod(i, nx) : (i < 0 ? 0 : nx - 1);
+    if (i < 0 || i >= nx) {
+        int bc = P->bc[i < 0 ? 0 : 1];
+        if (bc == BC_PERIODIC) i = imod(i, nx);
+        else if (is_wall(bc)) i = i < 0 ? -1 - i : 2 * nx - 1 - i;
+        else i = i < 0 ? 0 : nx - 1;
+    }
     return c->sy[(size_t)g * nx + i];
 }
 
@@ -479,11 +517,15 @@ static int kinetic_point(const Ctx *c, const Side *L, const Side *R, double dt, 
 
     /* collision time */
     double tau = 0.0;
-    if (P->tau_mode == 1) {
-        double pl, pr, dum1, dum2;
+    if (P->tau_mode == 1 || P->tau_mode == 2) {
+        double pl, pr, p0, dum1, dum2;
         pressure_mach(c, L->D[0], &pl, &dum1, &dum2);
         pressure_mach(c, R->D[0], &pr, &dum1, &dum2);
-        tau = P->c1 * dt + P->c2 * fabs(pl - pr) / (pl + pr) * dt;
+        /* inviscid: c1 dt; viscous (Sec. 4): mu / p at the face point, p of
+           the equilibrium state W0 there */
+        pressure_mach(c, Q0, &p0, &dum1, &dum2);
+        double base = P->tau_mode == 1 ? P->c1 * dt : P->mu / p0;
+        tau = base + P->c2 * fabs(pl - pr) / (pl + pr) * dt;
     }
 
     /* Eq. 2.6 term by term: (moment source, range, micro-slope factor) */
