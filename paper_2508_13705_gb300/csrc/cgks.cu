@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -69,7 +70,7 @@ Kfns pick_kfns(int dim, int order, int prec, int tau_mode)
     else if (prec == CGKS_FP64) k = M == 2 ? kfns_2_2_d() : (M == 3 ? kfns_2_3_d() : kfns_2_4_d());
     else k = M == 2 ? kfns_2_2_f() : (M == 3 ? kfns_2_3_f() : kfns_2_4_f());
     // the flux instances of the mesh's collision-time mode
-    if (tau_mode == CGKS_TAU_HGKS)
+    if (tau_mode == CGKS_TAU_HGKS || tau_mode == CGKS_TAU_NS)
         for (int c = 0; c < 2; ++c) { k.flux1v[c] = k.flux1h[c]; k.flux2v[c] = k.flux2h[c]; }
     k.flux1 = k.flux1v[0];
     k.flux2 = k.flux2v[0];
@@ -199,12 +200,15 @@ int validate(const cgks_params* p)
     if (p->dim != 1 && p->dim != 2) return CGKS_EINVAL;
     if (p->order != 5 && p->order != 7 && p->order != 9) return CGKS_EINVAL;
     if (p->precision != CGKS_FP64 && p->precision != CGKS_FP32_BULK) return CGKS_EINVAL;
-    if (p->tau_mode != CGKS_TAU_ZERO && p->tau_mode != CGKS_TAU_HGKS) return CGKS_EINVAL;
+    if (p->tau_mode != CGKS_TAU_ZERO && p->tau_mode != CGKS_TAU_HGKS && p->tau_mode != CGKS_TAU_NS)
+        return CGKS_EINVAL;
+    if (!(p->mu >= 0.0) || !std::isfinite(p->mu) || (p->tau_mode == CGKS_TAU_NS && !(p->mu > 0.0)))
+        return CGKS_EINVAL;
     if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->sigma_thres > 0.0)) return CGKS_EINVAL;
     if (!(p->gamma_hi > 0.0 && p->gamma_hi < 1.0) || !(p->gamma_lo > 0.0 && p->gamma_lo < 1.0)) return CGKS_EINVAL;
     if (!(p->weno_eps > 0.0)) return CGKS_EINVAL;
     for (int s = 0; s < 4; ++s) {
-        if (p->bc[s] < 0 || p->bc[s] > 2) return CGKS_EINVAL;
+        if (p->bc[s] < 0 || p->bc[s] > CGKS_BC_NOSLIP) return CGKS_EINVAL;
         if (p->bc[s] == CGKS_BC_FIXED && (p->dim == 2 || s >= 2)) return CGKS_EINVAL;
     }
     return CGKS_OK;
@@ -255,6 +259,10 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
     for (int k = 0; k < n; ++k) {
         if (nx[k] < 1 || ny[k] < 1 || (p->dim == 1 && ny[k] != 1)) return CGKS_EINVAL;
         if (!(ext[4 * k + 1] > ext[4 * k]) || (p->dim == 2 && !(ext[4 * k + 3] > ext[4 * k + 2]))) return CGKS_EINVAL;
+        // a wall mirrors up to 3 ghost layers onto distinct interior cells
+        bool wx = p->bc[0] >= CGKS_BC_REFLECTIVE || p->bc[1] >= CGKS_BC_REFLECTIVE;
+        bool wy = p->dim == 2 && (p->bc[2] >= CGKS_BC_REFLECTIVE || p->bc[3] >= CGKS_BC_REFLECTIVE);
+        if ((wx && nx[k] < 3) || (wy && ny[k] < 3)) return CGKS_EINVAL;
         // the kernels index a mesh's work items in 32 bits
         for (int kind = 0; kind < W_COUNT; ++kind)
             if (items(kind, p->dim, (p->order - 1) / 2, nx[k], ny[k]) >= (1LL << 31)) return CGKS_EINVAL;
@@ -303,6 +311,7 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         g.eps = p->weno_eps; g.c1 = p->tau_c1; g.c2 = p->tau_c2; g.cfl = p->cfl;
         g.gf = (float)g.gamma; g.Kf = (float)g.K; g.c1f = (float)g.c1; g.c2f = (float)g.c2;
         g.idx = 1.0 / g.dx; g.idy = 1.0 / g.dy;
+        g.mu = p->mu; g.muf = (float)p->mu;
         g.idxf = (float)g.idx; g.idyf = (float)g.idy;
         g.plane = (long long)nx[k] * ny[k];
         char* m0 = b->slab + base[k];
@@ -956,6 +965,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     if (p->dim != 1) return CGKS_EINVAL;
     if (p->bc[0] == CGKS_BC_FIXED || p->bc[1] == CGKS_BC_FIXED) return CGKS_ENOTSUP;
     if (nx < 1 || nx > CGKS_NOALLOC_MAX_CELLS || !(x1 > x0)) return CGKS_EINVAL;
+    if ((p->bc[0] >= CGKS_BC_REFLECTIVE || p->bc[1] >= CGKS_BC_REFLECTIVE) && nx < 3) return CGKS_EINVAL;
     if (!state_in || !state_out || !sigma_out) return CGKS_EINVAL;
     int dev = 0;
     CK(cudaGetDevice(&dev));
@@ -983,6 +993,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     g.cfl = p->cfl; g.plane = nx;
     g.gf = (float)g.gamma; g.Kf = (float)g.K; g.c1f = (float)g.c1; g.c2f = (float)g.c2;
     g.idx = 1.0 / g.dx; g.idy = 1.0;
+    g.mu = p->mu; g.muf = (float)p->mu;
     g.idxf = (float)g.idx; g.idyf = 1.0f;
     g.S0 = state_out;
     g.S1 = (double*)(base + oS1);

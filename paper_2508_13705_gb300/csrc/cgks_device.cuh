@@ -33,7 +33,7 @@
 
 namespace cgks {
 
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_FIXED = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_FIXED = 2, BC_REFLECTIVE = 3, BC_NOSLIP = 4 };
 enum { ST_S0 = 0, ST_S1 = 1, ST_S2 = 2, ST_R5 = 3, ST_R7 = 4, ST_R9 = 5 };
 enum { STATUS_NONPHYS = 1u };
 
@@ -64,6 +64,8 @@ struct Mesh {
     int tau_mode;
     double dx, dy, gamma, K, thr, ghi, glo, eps, c1, c2, cfl;
     double idx, idy;                // 1 / dx, 1 / dy
+    double mu;                      // dynamic viscosity (tau_mode 2)
+    float muf;
     float gf, Kf, c1f, c2f, idxf, idyf;  // FP32-bulk copies (no per-point conversions)
     long long plane;                // nx * ny
     // state: planes of nx*ny doubles.  2-D: W[4] Wx[4] Wy[4] Wxl[m][4] Wyl[m][4];
@@ -118,6 +120,7 @@ template <> struct MeshR<double> {
     __device__ static double K(const Mesh& g) { return g.K; }
     __device__ static double c1(const Mesh& g) { return g.c1; }
     __device__ static double c2(const Mesh& g) { return g.c2; }
+    __device__ static double mu(const Mesh& g) { return g.mu; }
     __device__ static double ih(const Mesh& g, int dir) { return dir == 0 ? g.idx : g.idy; }
     __device__ static double dt(const Mesh& g) { return *g.dt; }
 };
@@ -126,6 +129,7 @@ template <> struct MeshR<float> {
     __device__ static float K(const Mesh& g) { return g.Kf; }
     __device__ static float c1(const Mesh& g) { return g.c1f; }
     __device__ static float c2(const Mesh& g) { return g.c2f; }
+    __device__ static float mu(const Mesh& g) { return g.muf; }
     __device__ static float ih(const Mesh& g, int dir) { return dir == 0 ? g.idxf : g.idyf; }
     __device__ static float dt(const Mesh& g) { return *g.dtf; }
 };
@@ -142,11 +146,25 @@ template <> __device__ __forceinline__ const float* state_planes<float>(const Me
     return which == 0 ? g.F0 : g.F1;
 }
 
+__device__ __forceinline__ bool is_wall(int bc) { return bc == BC_REFLECTIVE || bc == BC_NOSLIP; }
+
+// Sign of a ghost value mirrored across a wall with normal x (normal = 0) or
+// y (normal = 1): reflection maps q to S q(-x), S reversing the normal
+// momentum (slip wall) or every momentum component (no-slip wall); a
+// derivative along the normal takes one more sign.
+template <int D>
+__device__ __forceinline__ bool wall_flip(int kind, int v, int normal, int bc)
+{
+    bool rev = (v == 1 + normal) || (bc == BC_NOSLIP && v >= 1 && v <= D);
+    bool dnormal = normal == 0 ? (kind == 1 || kind == 3) : (kind == 2 || kind == 4);
+    return rev != dnormal;
+}
+
 // kind: 0 W, 1 Wx, 2 Wy, 3 Wx_line, 4 Wy_line (global orientation)
 template <int D, int M, typename T>
 __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, int l, int i, int j)
 {
-    bool zero = false;
+    bool zero = false, neg = false;
     if (i < 0 || i >= g.nx) {
         int side = i < 0 ? 0 : 1;
         int bc = g.bc[side];
@@ -155,14 +173,24 @@ __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, in
         } else if (bc == BC_FIXED) {
             int layer = side == 0 ? (-1 - i) : (i - g.nx);
             return (T)g.ghost[((side * 3 + layer) * 2 + (kind == 0 ? 0 : 1)) * 3 + v];
+        } else if (is_wall(bc)) {
+            // ghost cell -1-k mirrors cell k; lines across x (Wy_line) swap ends
+            i = i < 0 ? -1 - i : 2 * g.nx - 1 - i;
+            neg = wall_flip<D>(kind, v, 0, bc);
+            if (kind == 4) l = M - 1 - l;
         } else {
             i = i < 0 ? 0 : g.nx - 1;
             zero = (kind == 1 || kind == 3);
         }
     }
     if (D == 2 && (j < 0 || j >= g.ny)) {
-        if (g.bc[j < 0 ? 2 : 3] == BC_PERIODIC) {
+        int bc = g.bc[j < 0 ? 2 : 3];
+        if (bc == BC_PERIODIC) {
             j = imod(j, g.ny);
+        } else if (is_wall(bc)) {
+            j = j < 0 ? -1 - j : 2 * g.ny - 1 - j;
+            neg = neg != wall_flip<D>(kind, v, 1, bc);
+            if (kind == 3) l = M - 1 - l;
         } else {
             j = j < 0 ? 0 : g.ny - 1;
             zero = zero || (kind == 2 || kind == 4);
@@ -182,7 +210,8 @@ __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, in
         default: p = 12 + 4 * M + 4 * l + v; break;
         }
     }
-    return S[p * g.plane + idx];
+    T val = S[p * g.plane + idx];
+    return neg ? -val : val;
 }
 
 // sigma of x-face f (between cells f-1 and f) in row j; ghost faces: periodic
@@ -191,21 +220,34 @@ template <int D>
 __device__ __forceinline__ double sigx(const Mesh& g, const double* sx, int f, int j)
 {
     if (f < 0 || f > g.nx) {
-        if (g.bc[f < 0 ? 0 : 1] != BC_PERIODIC) return 0.0;
-        f = imod(f, g.nx);
+        int bc = g.bc[f < 0 ? 0 : 1];
+        if (bc == BC_PERIODIC) f = imod(f, g.nx);
+        else if (is_wall(bc)) f = f < 0 ? -f : 2 * g.nx - f;  // beyond a wall: the mirrored face
+        else return 0.0;
     }
-    if (D == 2 && (j < 0 || j >= g.ny))
-        j = g.bc[j < 0 ? 2 : 3] == BC_PERIODIC ? imod(j, g.ny) : (j < 0 ? 0 : g.ny - 1);
+    if (D == 2 && (j < 0 || j >= g.ny)) {
+        int bc = g.bc[j < 0 ? 2 : 3];
+        if (bc == BC_PERIODIC) j = imod(j, g.ny);
+        else if (is_wall(bc)) j = j < 0 ? -1 - j : 2 * g.ny - 1 - j;
+        else j = j < 0 ? 0 : g.ny - 1;
+    }
     return sx[(long long)j * (g.nx + 1) + f];
 }
 
 __device__ __forceinline__ double sigy(const Mesh& g, const double* sy, int i, int f)
 {
     if (f < 0 || f > g.ny) {
-        if (g.bc[f < 0 ? 2 : 3] != BC_PERIODIC) return 0.0;
-        f = imod(f, g.ny);
+        int bc = g.bc[f < 0 ? 2 : 3];
+        if (bc == BC_PERIODIC) f = imod(f, g.ny);
+        else if (is_wall(bc)) f = f < 0 ? -f : 2 * g.ny - f;
+        else return 0.0;
     }
-    if (i < 0 || i >= g.nx) i = g.bc[i < 0 ? 0 : 1] == BC_PERIODIC ? imod(i, g.nx) : (i < 0 ? 0 : g.nx - 1);
+    if (i < 0 || i >= g.nx) {
+        int bc = g.bc[i < 0 ? 0 : 1];
+        if (bc == BC_PERIODIC) i = imod(i, g.nx);
+        else if (is_wall(bc)) i = i < 0 ? -1 - i : 2 * g.nx - 1 - i;
+        else i = i < 0 ? 0 : g.nx - 1;
+    }
     return sy[(long long)f * g.nx + i];
 }
 

@@ -562,7 +562,10 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
             Wtt[v] = -S2[v];
         }
         if (hgks) {
-            R tau = MeshR<R>::c1(g) * Dt + MeshR<R>::c2(g) * fabs(pz[0] - pz[1]) / (pz[0] + pz[1]) * Dt;
+            // inviscid: c1 dt; viscous (Sec. 4): mu / p with p the pressure of
+            // the equilibrium state at the face point
+            R base = g.tau_mode == 2 ? MeshR<R>::mu(g) / (M0.rho * M0.il) : MeshR<R>::c1(g) * Dt;
+            R tau = base + MeshR<R>::c2(g) * fabs(pz[0] - pz[1]) / (pz[0] + pz[1]) * Dt;
             // collision and non-equilibrium terms of Eq. 2.6, fitted analytically
             R Att[4], T2[4], T3[4], T4[4];
 #pragma unroll
@@ -834,7 +837,8 @@ __global__ void __launch_bounds__(256) k_convert(Work w, int to_float)
 }
 
 // -------------------------------------------------------------- CFL (Sec. 4)
-// max over cells of (|U| + a) / min(dx, dy); one atomicMax per block on the
+// max over cells of (|U| + a) / h (and 4 nu / h^2 for viscous flow), h =
+// min(dx, dy); one atomicMax per block on the
 // bit pattern of a positive double (ordered like the value).  The plain form
 // evaluates the speeds in FP64 from the FP64 averages; the FP32-bulk form in
 // FP32 from its float state planes (the step size is not a conserved
@@ -864,7 +868,10 @@ __global__ void __launch_bounds__(256) k_cfl(Work w)
         R q2 = mu * mu + mv * mv;
         R p = (gm - (R)1) * (E - (R)0.5 * rho * q2);
         R ih = D == 2 ? fmax(MeshR<R>::ih(g, 0), MeshR<R>::ih(g, 1)) : MeshR<R>::ih(g, 0);  // 1 / min(dx, dy)
-        double s = (double)((sqrt(q2) + sqrt(gm * p * ir)) * ih);
+        R sp = (sqrt(q2) + sqrt(gm * p * ir)) * ih;
+        // viscous flow: the diffusive limit dt <= h^2 / (4 nu), nu = mu / rho
+        if (g.tau_mode == 2) sp = fmax(sp, (R)4 * MeshR<R>::mu(g) * ir * ih * ih);
+        double s = (double)sp;
         if (!(s == s)) s = 1e300;  // a NaN state yields a tiny step and is flagged by the stages
         best = fmax(best, s);
     }
