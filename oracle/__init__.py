@@ -39,6 +39,7 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 
 BC_PERIODIC, BC_TRANSMISSIVE, BC_FIXED, BC_REFLECTIVE, BC_NOSLIP = 0, 1, 2, 3, 4
 TAU_ZERO, TAU_HGKS, TAU_NS = 0, 1, 2
+DFF_LAG_STEP, DFF_LAG_STAGE = 0, 1
 
 
 def build(force=False):
@@ -107,7 +108,7 @@ class Oracle:
 
     def __init__(self, dim, order, nx, ny=1, extent=(0.0, 1.0, 0.0, 1.0), gamma=1.4, cfl=0.5,
                  tau_mode=TAU_ZERO, bc=(BC_PERIODIC,) * 4, sigma_thres=1.0, gamma_hi=0.85,
-                 gamma_lo=0.6, weno_eps=1e-8, c1=0.05, c2=1.0, step3=0, mu=0.0):
+                 gamma_lo=0.6, weno_eps=1e-8, c1=0.05, c2=1.0, step3=0, mu=0.0, dff_lag=DFF_LAG_STAGE):
         assert dim in (1, 2) and order in (5, 7, 9)
         self.dim, self.order, self.nx, self.ny = dim, order, nx, (ny if dim == 2 else 1)
         self.nv = dim + 2
@@ -129,6 +130,10 @@ class Oracle:
         P.weno_eps, P.c1, P.c2 = weno_eps, c1, c2
         P.mu = mu
         self.mu, self.tau_mode = mu, tau_mode
+        # reading of the DFF time lag (Sec. 3.1): sigma of stage 1 of step n-1
+        # in both stages of step n (STEP), or in stage 2 the sigma of stage 1 of
+        # the same step (STAGE)
+        self.dff_lag = dff_lag
         self.P = P
         tabs = coeffs.poly_tables()
         self.T = np.ascontiguousarray(np.stack([tabs[k] for k in ("S0", "S1", "S2", "r5", "r7", "r9")]))
@@ -323,6 +328,10 @@ class Oracle:
             Wys = Wxls = Wyls = None
             sig_x_new = r1[1].reshape(1, -1)
         # ---- stage 2 at t* (same dt)
+        if self.dff_lag == DFF_LAG_STAGE:
+            self.sx = np.ascontiguousarray(sig_x_new)
+            if self.dim == 2:
+                self.sy = np.ascontiguousarray(sig_y_new)
         r2 = self.faces(dt, state=(np.ascontiguousarray(Ws), np.ascontiguousarray(Wxs),
                                    None if Wys is None else np.ascontiguousarray(Wys), Wxls, Wyls))
         Fd2, Fh2, W02, Wh2, Wd2 = r2[0]

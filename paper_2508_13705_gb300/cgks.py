@@ -19,6 +19,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libcgks.so")
 
 FP64, FP32_BULK = 0, 1
 TAU_ZERO, TAU_HGKS, TAU_NS = 0, 1, 2
+DFF_LAG_STEP, DFF_LAG_STAGE = 0, 1
 BC_PERIODIC, BC_TRANSMISSIVE, BC_FIXED, BC_REFLECTIVE, BC_NOSLIP = 0, 1, 2, 3, 4
 EINVAL, ENOMEM, ECUDA, ENONPHYS, ETIMEOUT, ENOTSUP = -1, -2, -3, -4, -5, -6
 
@@ -36,7 +37,7 @@ class Params(ctypes.Structure):
                 ("tau_mode", ctypes.c_int), ("bc", ctypes.c_int * 4), ("gamma", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("sigma_thres", ctypes.c_double), ("gamma_hi", ctypes.c_double),
                 ("gamma_lo", ctypes.c_double), ("weno_eps", ctypes.c_double), ("tau_c1", ctypes.c_double),
-                ("tau_c2", ctypes.c_double), ("mu", ctypes.c_double)]
+                ("tau_c2", ctypes.c_double), ("mu", ctypes.c_double), ("dff_lag", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -204,6 +204,7 @@ int validate(const cgks_params* p)
         return CGKS_EINVAL;
     if (!(p->mu >= 0.0) || !std::isfinite(p->mu) || (p->tau_mode == CGKS_TAU_NS && !(p->mu > 0.0)))
         return CGKS_EINVAL;
+    if (p->dff_lag != CGKS_DFF_LAG_STEP && p->dff_lag != CGKS_DFF_LAG_STAGE) return CGKS_EINVAL;
     if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->sigma_thres > 0.0)) return CGKS_EINVAL;
     if (!(p->gamma_hi > 0.0 && p->gamma_hi < 1.0) || !(p->gamma_lo > 0.0 && p->gamma_lo < 1.0)) return CGKS_EINVAL;
     if (!(p->weno_eps > 0.0)) return CGKS_EINVAL;
@@ -305,6 +306,7 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         g.nx = nx[k]; g.ny = ny[k]; g.order = p->order; g.oi = (p->order - 5) / 2;
         for (int s = 0; s < 4; ++s) g.bc[s] = p->bc[s];
         g.tau_mode = p->tau_mode;
+        g.dff_lag = p->dff_lag;
         g.dx = (ext[4 * k + 1] - ext[4 * k]) / nx[k];
         g.dy = p->dim == 2 ? (ext[4 * k + 3] - ext[4 * k + 2]) / ny[k] : 1.0;
         g.gamma = p->gamma; g.K = K; g.thr = p->sigma_thres; g.ghi = p->gamma_hi; g.glo = p->gamma_lo;
@@ -621,6 +623,7 @@ int cgks_default_params(cgks_params* p, int dim, int order)
     p->weno_eps = 1e-8;
     p->tau_c1 = 0.05;
     p->tau_c2 = 1.0;
+    p->dff_lag = CGKS_DFF_LAG_STAGE;
     return CGKS_OK;
 }
 
@@ -987,6 +990,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     g.nx = nx; g.ny = 1; g.order = p->order; g.oi = (p->order - 5) / 2;
     for (int q = 0; q < 4; ++q) g.bc[q] = p->bc[q];
     g.tau_mode = p->tau_mode;
+    g.dff_lag = p->dff_lag;
     g.dx = (x1 - x0) / nx; g.dy = 1.0;
     g.gamma = p->gamma; g.K = (3.0 - p->gamma) / (p->gamma - 1.0); g.thr = p->sigma_thres;
     g.ghi = p->gamma_hi; g.glo = p->gamma_lo; g.eps = p->weno_eps; g.c1 = p->tau_c1; g.c2 = p->tau_c2;

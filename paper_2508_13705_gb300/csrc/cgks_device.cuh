@@ -62,6 +62,7 @@ struct Mesh {
     int nx, ny, order, oi;          // oi: 0, 1, 2 for orders 5, 7, 9
     int bc[4];
     int tau_mode;
+    int dff_lag;                    // 0: sigma of step n-1; 1: stage 2 uses stage 1's
     double dx, dy, gamma, K, thr, ghi, glo, eps, c1, c2, cfl;
     double idx, idy;                // 1 / dx, 1 / dy
     double mu;                      // dynamic viscosity (tau_mode 2)

@@ -114,6 +114,11 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         if (dir == 0) { unsigned d = na + 6, q = li / d; a = (int)(li - q * d) - 3; b = (int)q - 1; }
         else { unsigned d = nb + 2, q = li / d; b = (int)(li - q * d) - 1; a = (int)q - 3; }
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
+        // sigma of the DFF (Sec. 3.1): of step n-1 in both stages, or, in stage 2
+        // of the stage-lag reading, the face means of stage 1 of this step
+        const bool lag_stage = stage == 2 && g.dff_lag;
+        const double* SX = lag_stage ? g.sig_xn : g.sig_x;
+        const double* SY = lag_stage ? g.sig_yn : g.sig_y;
         // the tangential stencil: a direct walk for interior cells, whose loads
         // are issued before the DFF selections so that their latencies overlap
         bool inner = a >= 0 && a < na && b >= 2 && b + 2 < nb;
@@ -146,14 +151,14 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         // face sigma of the tangential stencil: a direct walk for interior cells
         double s6[6];
         if (inner) {
-            const double* sp = dir == 0 ? g.sig_y + (long long)(b - 2) * g.nx + a
-                                        : g.sig_x + (long long)a * (g.nx + 1) + (b - 2);
+            const double* sp = dir == 0 ? SY + (long long)(b - 2) * g.nx + a
+                                        : SX + (long long)a * (g.nx + 1) + (b - 2);
             const long long ss = dir == 0 ? g.nx : 1;
 #pragma unroll
             for (int q = 0; q < 6; ++q) s6[q] = sp[q * ss];
         } else {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) s6[q] = lsigT(g, g.sig_x, g.sig_y, dir, a, b - 2 + q);
+            for (int q = 0; q < 6; ++q) s6[q] = lsigT(g, SX, SY, dir, a, b - 2 + q);
         }
         DffR<R> dff = dff_r<R>(dff_select(g.order, s6, g.thr));
         R ht = (R)(dir == 0 ? g.dy : g.dx);
@@ -166,14 +171,14 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         if (a >= -1 && a <= na) {
             double n6[6];
             if (a >= 2 && a + 3 <= na && b >= 0 && b < nb) {
-                const double* sp = dir == 0 ? g.sig_x + (long long)b * (g.nx + 1) + (a - 2)
-                                            : g.sig_y + (long long)(a - 2) * g.nx + b;
+                const double* sp = dir == 0 ? SX + (long long)b * (g.nx + 1) + (a - 2)
+                                            : SY + (long long)(a - 2) * g.nx + b;
                 const long long ss = dir == 0 ? 1 : g.nx;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) n6[q] = sp[q * ss];
             } else {
 #pragma unroll
-                for (int q = 0; q < 6; ++q) n6[q] = lsigN<2>(g, g.sig_x, g.sig_y, dir, a - 2 + q, b);
+                for (int q = 0; q < 6; ++q) n6[q] = lsigN<2>(g, SX, SY, dir, a - 2 + q, b);
             }
             R pk[4];
             dff_pack<R>(dff_r<R>(dff_select(g.order, n6, g.thr)), pk);
@@ -240,7 +245,10 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         } else {
             double s6[6];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) s6[q] = sigx<1>(g, g.sig_x, a - 2 + q, 0);
+            // sigma of the DFF: step n-1, or in stage 2 of the stage-lag reading the
+            // face means of stage 1 of this step
+            const double* SX = (stage == 2 && g.dff_lag) ? g.sig_xn : g.sig_x;
+            for (int q = 0; q < 6; ++q) s6[q] = sigx<1>(g, SX, a - 2 + q, 0);
             dff = dff_r<R>(dff_select(g.order, s6, g.thr));
         }
         {
