@@ -640,6 +640,19 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
 }
 
 // -------------------------------------------------------------- update (2-D)
+// r - l exactly, as a double: in FP64 the difference itself; in FP32 the
+// rounded difference plus its rounding error (Knuth's two-sum), each exact
+// in a double.
+__device__ __forceinline__ double exact_diff(double r, double l) { return r - l; }
+__device__ __forceinline__ double exact_diff(float r, float l)
+{
+    float b = -l;
+    float s = r + b;
+    float z = s - r;
+    float e = (r - (s - z)) + (b - z);
+    return (double)s + (double)e;
+}
+
 // Stage 1 writes W* (S1) and the accumulator; stage 2 writes state n+1 (S0).
 // FP32-bulk form: the float planes (F1 / F0) receive everything the next stage
 // reads, the FP64 planes the cell averages of state n+1 (W* lives in F1 only).
@@ -668,9 +681,14 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
         R* accs = (R*)(g.ACC + 4 * P);
         float* outf = STAGE == 1 ? g.F1 : g.F0;
         const auto& TR = Tab<R>::get(g.oi);
-        // face differences and Gauss sums in the bulk precision (the face data
-        // are bulk values); the cell averages accumulate in FP64 below
-        R fx0[4] = {0, 0, 0, 0}, fy0[4] = {0, 0, 0, 0}, fx1[4] = {0, 0, 0, 0}, fy1[4] = {0, 0, 0, 0};
+        // Conserved quantities: the Gauss sum over a face's points is formed
+        // per face, in the bulk precision and in the same order by both cells
+        // of the face (bitwise alike), and the difference of a cell's two
+        // face sums is taken exactly (exact_diff) into the FP64 averages, so
+        // the updates telescope over the mesh and the totals change only by
+        // the boundary fluxes and FP64 rounding.  Slopes use bulk differences.
+        R gxr0[4] = {0, 0, 0, 0}, gxl0[4] = {0, 0, 0, 0}, gyr0[4] = {0, 0, 0, 0}, gyl0[4] = {0, 0, 0, 0};
+        R gxr1[4] = {0, 0, 0, 0}, gxl1[4] = {0, 0, 0, 0}, gyr1[4] = {0, 0, 0, 0}, gyl1[4] = {0, 0, 0, 0};
         R sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
 #pragma unroll 1
         for (int l = 0; l < M; ++l) {
@@ -689,11 +707,11 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
                     R dx_ = a[v] - bq[v];
                     R dy_ = cq[v] - dq[v];
                     if (q == 0) {
-                        fx0[v] += wl * dx_;
-                        fy0[v] += wl * dy_;
+                        gxr0[v] += wl * a[v]; gxl0[v] += wl * bq[v];
+                        gyr0[v] += wl * cq[v]; gyl0[v] += wl * dq[v];
                     } else if (STAGE == 1 && q == 1) {
-                        fx1[v] += wl * dx_;
-                        fy1[v] += wl * dy_;
+                        gxr1[v] += wl * a[v]; gxl1[v] += wl * bq[v];
+                        gyr1[v] += wl * cq[v]; gyl1[v] += wl * dq[v];
                     } else if ((STAGE == 1 && q == 2) || (STAGE == 2 && q == 1)) {
                         R lx = dx_ * ridx, ly = dy_ * ridy;
                         if (STAGE == 2) {
@@ -720,12 +738,13 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             double Wn;
+            const double dx0 = exact_diff(gxr0[v], gxl0[v]), dy0 = exact_diff(gyr0[v], gyl0[v]);
             if (STAGE == 1) {
                 double W = g.S0[v * P + c];
-                Wn = W - (double)fx0[v] * idx - (double)fy0[v] * idy;               // Eq. 2.21
-                g.ACC[v * P + c] = W - (double)fx1[v] * idx - (double)fy1[v] * idy;
+                Wn = W - dx0 * idx - dy0 * idy;                                              // Eq. 2.21
+                g.ACC[v * P + c] = W - exact_diff(gxr1[v], gxl1[v]) * idx - exact_diff(gyr1[v], gyl1[v]) * idy;
             } else {
-                Wn = g.ACC[v * P + c] - (double)fx0[v] * idx - (double)fy0[v] * idy;  // Eq. 2.22-2.23
+                Wn = g.ACC[v * P + c] - dx0 * idx - dy0 * idy;  // Eq. 2.22-2.23
             }
             // the FP32-bulk stage 2 reads W* from the float planes only
             if (!BULK32 || STAGE == 2) out[v * P + c] = Wn;
