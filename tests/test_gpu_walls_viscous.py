@@ -1,0 +1,206 @@
+"""Wall boundaries, viscous flow and the stage-lag DFF reading on the GPU
+(Sec. 3.1, 4, 4.4, 4.9): per-step parity with the FP64 oracle, the
+mirrored-periodic equivalence of a wall run on the device, conservation,
+the shear-wave decay rate of the viscous collision time, a strong shock tube
+against its exact solution, and the viscous shock tube."""
+import numpy as np
+import pytest
+
+import exact_riemann as er
+import oracle
+from paper_2508_13705_gb300 import cgks, inputs
+from test_gpu_parity import FIELDS_1D, FIELDS_2D, compare
+from test_oracle_walls_viscous import mirror_double, shear_wave, wall_impact_1d
+
+pytestmark = pytest.mark.gpu
+REFL, NOSLIP = cgks.BC_REFLECTIVE, cgks.BC_NOSLIP
+STRONG_TUBE = ((120.0, 0.0, 120.0 / 1.4), (1.2, 0.0, 1.2 / 1.4))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2508_13705_gb300 import build
+    build.build()
+    oracle.build()
+
+
+def per_step(dim, order, nx, ny, st, steps, extent, what, sigma_floor=1e-14, **kw):
+    okw = {k: v for k, v in kw.items() if k in ("tau_mode", "bc", "cfl", "gamma", "mu", "dff_lag")}
+    o = oracle.Oracle(dim, order, nx, ny, extent=extent, **okw)
+    o.set_state(*st)
+    s = cgks.Solver(dim, order, nx, ny, extent=extent, **kw)
+    fields = FIELDS_2D if dim == 2 else FIELDS_1D
+    for k in range(steps):
+        g0 = o.get_state()
+        if dim == 2:
+            s.set_state(g0["W"], g0["Wx"], g0["Wy"], g0["Wx_line"], g0["Wy_line"], g0["sigma_x"], g0["sigma_y"])
+        else:
+            s.set_state(g0["W"], g0["Wx"], sigma_x=g0["sigma_x"])
+        dt = o.compute_dt()
+        s.step(dt)
+        s.sync()
+        o.step(dt)
+        assert o.flags == 0
+        compare(s.get_state(), o, fields, what="%s step %d" % (what, k), sigma_floor=sigma_floor)
+    s.close()
+
+
+@pytest.mark.parametrize("order", [5, 9])
+def test_wall_impact_1d_per_step(order):
+    """Gas driven supersonically into a slip wall (shock reflection) and away
+    from the other (strong rarefaction)."""
+    per_step(1, order, 100, 1, wall_impact_1d(100), 30, (0, 1, 0, 1), "wall impact", sigma_floor=1e-13,
+             tau_mode=cgks.TAU_HGKS, bc=(REFL,) * 4)
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_walls_2d_per_step_and_mirror_equivalence(axis):
+    """Quadrant data between two slip walls (periodic the other way): per-step
+    parity with the oracle, then the GPU wall run against the GPU run of the
+    doubled periodic problem, which does not use the ghost rule."""
+    nx, ny, order = 12, 10, 9
+    st = [a[..., :ny, :nx] for a in inputs.quadrants_2d(12, order, seed=3)]
+    rng = np.random.default_rng(5)
+    st = [st[0]] + [0.02 * rng.standard_normal(a.shape) for a in st[1:]]
+    bc = [cgks.BC_PERIODIC] * 4
+    bc[2 * axis] = bc[2 * axis + 1] = REFL
+    kw = dict(tau_mode=cgks.TAU_HGKS, bc=tuple(bc))
+    per_step(2, order, nx, ny, st, 3, (0, 1, 0, 1), "walls axis %d" % axis, **kw)
+    sw = cgks.Solver(2, order, nx, ny, extent=(0, 1, 0, 1), **kw)
+    sw.set_state(*st)
+    dbl = mirror_double(st, axis, 4)
+    ext = (0, 2, 0, 1) if axis == 0 else (0, 1, 0, 2)
+    sp = cgks.Solver(2, order, nx * (2 - axis), ny * (1 + axis), extent=ext, tau_mode=cgks.TAU_HGKS)
+    sp.set_state(*dbl)
+    for _ in range(3):
+        dt = sp.compute_dt()
+        sw.step(dt)
+        sp.step(dt)
+    a, b = sw.get_state(), sp.get_state()
+    half = (Ellipsis, slice(0, nx)) if axis == 0 else (Ellipsis, slice(0, ny), slice(None))
+    for f in ("W", "Wx", "Wy", "Wx_line", "Wy_line"):
+        bh = b[f][half]
+        assert np.abs(a[f] - bh).max() <= 1e-11 * max(1.0, np.abs(bh).max()), f
+    sw.close()
+    sp.close()
+
+
+def test_conservation_on_gpu():
+    """Configuration 2 (Sec. 4.7) for 100 steps.  Between slip walls on all
+    four sides (FP64): mass and energy stay constant to FP64 rounding.  In a
+    periodic box the FP32-bulk form conserves them to FP64 rounding as well:
+    each face's Gauss-summed flux is formed alike by both of its cells and
+    the difference enters the FP64 averages exactly, so the updates
+    telescope."""
+    n = 64
+    states, split = inputs.CONFIG2
+    st = inputs.quadrants_2d(n, 7, states=states, split=split)
+    m0 = st[0].sum(axis=(1, 2))
+    for prec, bc in ((cgks.FP64, (REFL,) * 4), (cgks.FP32_BULK, (cgks.BC_PERIODIC,) * 4)):
+        s = cgks.Solver(2, 7, n, n, extent=(0, 1, 0, 1), precision=prec, tau_mode=cgks.TAU_HGKS, bc=bc)
+        s.set_state(*st)
+        s.advance(100, 0.0)
+        s.sync()
+        m1 = s.get_state()["W"].sum(axis=(1, 2))
+        for v in (0, 3):
+            assert abs(m1[v] - m0[v]) <= 1e-13 * abs(m0[v]), (prec, v, m1[v] - m0[v])
+        s.close()
+
+
+@pytest.mark.parametrize("walls", [False, True])
+def test_viscous_shear_wave_per_step_and_decay(walls):
+    """tau = mu / p: per-step parity with the oracle, then the GPU decay rate
+    of a small shear wave against nu k^2 (periodic, or between no-slip walls)."""
+    mu = 0.01
+    nx, ny = 32, 4
+    st, k, xc = shear_wave(nx, ny, 5, 1e-3, walls)
+    bc = (NOSLIP, NOSLIP, cgks.BC_PERIODIC, cgks.BC_PERIODIC) if walls else (cgks.BC_PERIODIC,) * 4
+    kw = dict(tau_mode=cgks.TAU_NS, bc=bc, mu=mu)
+    ext = (0, 1, 0, ny / nx)
+    per_step(2, 5, nx, ny, st, 3, ext, "shear wave", **kw)
+    s = cgks.Solver(2, 5, nx, ny, extent=ext, **kw)
+    s.set_state(*st)
+    t_end, t = 0.5, 0.0
+    while t < t_end - 1e-14:
+        dt = min(s.compute_dt(), t_end - t)
+        s.step(dt)
+        t += dt
+    s.sync()
+    v = s.get_state()["W"][2, 0]
+    s.close()
+    rate = -np.log((v * np.sin(k * xc)).sum() / (st[0][2, 0] * np.sin(k * xc)).sum()) / t_end
+    assert abs(rate / (mu * k * k) - 1) < 5e-3
+
+
+@pytest.mark.parametrize("order", [5, 9])
+def test_strong_shock_tube(order):
+    """Density and pressure ratio 100 under the stage-lag DFF reading: per-step
+    parity (the stage-2 sigma comes from stage 1 of the same step on both
+    sides), then a whole GPU run to t = 0.1 against the exact solution."""
+    N = 200
+    st = inputs.riemann_1d(N, *STRONG_TUBE)
+    kw = dict(tau_mode=cgks.TAU_HGKS, bc=(1, 1, 1, 1), cfl=0.2)
+    per_step(1, order, N, 1, st, 20, (0, 1, 0, 1), "strong tube", sigma_floor=1e-13, **kw)
+    s = cgks.Solver(1, order, N, extent=(0, 1, 0, 1), **kw)
+    s.set_state(*st)
+    t = 0.0
+    while t < 0.1 - 1e-14:
+        dt = min(s.compute_dt(), 0.1 - t)
+        s.step(dt)
+        t += dt
+    _, code, _ = s.sync(raise_on_error=False)
+    W = s.get_state()["W"]
+    s.close()
+    assert code == 0 and W[0].min() > 0
+    assert np.abs(W[0, 0] - er.cell_average_rho(*STRONG_TUBE, N, 0.1)).mean() < 0.5
+
+
+def viscous_shock_tube(nx, ny, order, gamma=1.4):
+    """Sec. 4.9: [0,1] x [0,0.5], (rho, u, p) = (120, 0, 120/gamma) left of
+    x = 0.5 and (1.2, 0, 1.2/gamma) right; zero slopes."""
+    xc = (np.arange(nx) + 0.5) / nx
+    left = (xc < 0.5)[None, :] * np.ones((ny, 1), dtype=bool)
+    rho = np.where(left, 120.0, 1.2)
+    p = rho / gamma
+    W = np.stack([rho, 0 * rho, 0 * rho, p / (gamma - 1)])
+    m = {5: 2, 7: 3, 9: 4}[order]
+    z = np.zeros_like(W)
+    return (W, z, z.copy(), np.zeros((m, 4, ny, nx)), np.zeros((m, 4, ny, nx)))
+
+
+# Re = 200 with mu = 1/Re (unit reference density, sound speed and length of
+# the low-pressure gas), no-slip walls left, right and below, a symmetry plane
+# above, CFL 0.2
+VST = dict(tau_mode=cgks.TAU_NS, mu=1.0 / 200, cfl=0.2, bc=(NOSLIP, NOSLIP, NOSLIP, REFL))
+
+
+@pytest.mark.parametrize("order", [5, 9])
+def test_viscous_shock_tube_per_step(order):
+    nx, ny = 40, 20
+    per_step(2, order, nx, ny, viscous_shock_tube(nx, ny, order), 4, (0, 1, 0, 0.5), "viscous shock tube",
+             sigma_floor=1e-13, **VST)
+
+
+def test_viscous_shock_tube_500x250_closed_box():
+    """The paper's mesh, FP32 bulk, order 5, to t = 0.2: positive throughout,
+    and the closed box keeps its mass and energy.  Interior fluxes telescope
+    exactly; at a wall the two mirrored face states are reconstructed from
+    different cells, so their fluxes cancel to FP32 rounding only, which over
+    the about 4000 steps leaves a drift of order 1e-6."""
+    nx, ny = 500, 250
+    st = viscous_shock_tube(nx, ny, 5)
+    s = cgks.Solver(2, 5, nx, ny, extent=(0, 1, 0, 0.5), precision=cgks.FP32_BULK, **VST)
+    s.set_state(*st)
+    t = 0.0
+    while t < 0.2 - 1e-14:
+        dt = min(s.compute_dt(), 0.2 - t)
+        s.step(dt)
+        t += dt
+    _, code, _ = s.sync(raise_on_error=False)
+    W = s.get_state()["W"]
+    s.close()
+    assert code == 0 and W[0].min() > 0
+    m0 = st[0].sum(axis=(1, 2))
+    m1 = W.sum(axis=(1, 2))
+    for v in (0, 3):
+        assert abs(m1[v] - m0[v]) <= 1e-5 * abs(m0[v])
