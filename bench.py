@@ -387,14 +387,7 @@ def accuracy_one(torch, cgks, order, stream, n, t_end):
     for name, prec in (("fp64", cgks.FP64), ("fp32", cgks.FP32_BULK)):
         s = cgks.Solver(2, order, n, n, extent=(0.0, 10.0, 0.0, 10.0), precision=prec, stream=stream.cuda_stream)
         s.set_state(*st)
-        t = 0.0
-        steps = 0
-        while t < t_end - 1e-12:
-            dt = min(s.compute_dt(), t_end - t)
-            s.step(dt)
-            t += dt
-            steps += 1
-        _, rc, _ = s.sync(raise_on_error=False)
+        t, steps, rc = s.run_to(t_end, max_steps=20000)
         W = s.get_state()["W"]
         out["l1_" + name] = float(np.abs(W[0] - st[0][0]).mean())
         out["status_" + name] = rc
@@ -511,15 +504,9 @@ def config3_bench(torch, cgks, stream, full_order=9):
     full = {}
     for prec, key in ((cgks.FP32_BULK, "fp32"), (cgks.FP64, "fp64")):
         s = solver(500, full_order, prec)
-        t, steps = 0.0, 0
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        while t < 0.6 - 1e-14:
-            dt = min(s.compute_dt(), 0.6 - t)
-            s.step(dt)
-            t += dt
-            steps += 1
-        _, rc, _ = s.sync(raise_on_error=False)
+        t, steps, rc = s.run_to(0.6, max_steps=20000)
         wall = time.perf_counter() - t0
         s.close()
         full[key] = {"steps": steps, "wall_s": round(wall, 3), "status": rc,

@@ -59,13 +59,15 @@ extern "C" {
                                 p the pressure of the equilibrium state at the face point;
                                 the time step adds the limit dx^2 / (4 nu), nu = mu / rho */
 /* time lag of the DFF's sigma (Sec. 3.1, "from the previous time step"): */
-#define CGKS_DFF_LAG_STEP 0  /* sigma of stage 1 of step n-1 in both stages of step n */
-#define CGKS_DFF_LAG_STAGE 1 /* (default) the same in stage 1; stage 2 uses the sigma of
-                                stage 1 of step n, half a step old.  With the step lag a
-                                strong wave that enters a cell within one step meets
-                                stencils that still see sigma = 0 (the Sec. 4.9 shock tube
-                                loses positivity in step 2); smooth data take the same
-                                branches under both */
+#define CGKS_DFF_LAG_STEP 0  /* (default) sigma of stage 1 of step n-1 in both stages of step n */
+#define CGKS_DFF_LAG_STAGE 1 /* the same in stage 1; stage 2 uses the sigma of stage 1 of
+                                step n, half a step old.  Neither carries every case: with
+                                the step lag a strong wave that enters a cell within one
+                                step meets stencils that still see sigma = 0 (the Sec. 4.9
+                                shock tube loses positivity in step 2), while the stage lag
+                                lets the two stages pick different stencils and loses
+                                positivity late in Configuration 3 (Sec. 4.7, 500^2, FP32
+                                bulk).  Smooth data take the same branches under both */
 /* boundary conditions, per side: bc[0..3] = x-low, x-high, y-low, y-high */
 #define CGKS_BC_PERIODIC 0
 #define CGKS_BC_TRANSMISSIVE 1  /* ghost = nearest interior cell, normal slopes zero */
@@ -92,7 +94,7 @@ typedef struct {
     double tau_c1;      /* c1 of the HGKS collision time (0.05) */
     double tau_c2;      /* c2 of the HGKS collision time (1.0) */
     double mu;          /* dynamic viscosity of CGKS_TAU_NS (constant), >= 0 */
-    int dff_lag;        /* CGKS_DFF_LAG_STAGE (default) or CGKS_DFF_LAG_STEP */
+    int dff_lag;        /* CGKS_DFF_LAG_STEP (default) or CGKS_DFF_LAG_STAGE */
 } cgks_params;
 
 typedef struct cgks_solver cgks_solver;
@@ -110,7 +112,7 @@ typedef struct {
 
 /* Fill *p with the paper's defaults for (dim, order): gamma 1.4, CFL 0.5,
  * sigma_thres 1, gamma_hi 0.85, gamma_lo 0.6, eps 1e-8, c1 0.05, c2 1, mu 0,
- * FP64, tau = 0, periodic, stage-lag DFF.  Returns CGKS_EINVAL for a NULL p. */
+ * FP64, tau = 0, periodic, step-lag DFF.  Returns CGKS_EINVAL for a NULL p. */
 int cgks_default_params(cgks_params* p, int dim, int order);
 
 /* Create a solver for an nx x ny mesh on [x0,x1] x [y0,y1] (1-D: ny = 1,

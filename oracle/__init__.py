@@ -108,7 +108,7 @@ class Oracle:
 
     def __init__(self, dim, order, nx, ny=1, extent=(0.0, 1.0, 0.0, 1.0), gamma=1.4, cfl=0.5,
                  tau_mode=TAU_ZERO, bc=(BC_PERIODIC,) * 4, sigma_thres=1.0, gamma_hi=0.85,
-                 gamma_lo=0.6, weno_eps=1e-8, c1=0.05, c2=1.0, step3=0, mu=0.0, dff_lag=DFF_LAG_STAGE):
+                 gamma_lo=0.6, weno_eps=1e-8, c1=0.05, c2=1.0, step3=0, mu=0.0, dff_lag=DFF_LAG_STEP):
         assert dim in (1, 2) and order in (5, 7, 9)
         self.dim, self.order, self.nx, self.ny = dim, order, nx, (ny if dim == 2 else 1)
         self.nv = dim + 2

@@ -203,6 +203,27 @@ class Solver:
     def step(self, dt=0.0):
         _check(lib().cgks_step(self.h, float(dt)), "cgks_step")
 
+    def run_to(self, t_end, t=0.0, max_steps=10 ** 6, check_every=64):
+        """Advance from time ``t`` to ``t_end`` with the CFL step, the last step
+        clipped.  Returns (t, steps, status).  Stops early when the device
+        status reports a non-physical state (checked every ``check_every``
+        steps and whenever the CFL step stops being positive and finite: a
+        blown-up state gives a vanishing step that would never reach t_end) or
+        after ``max_steps``."""
+        steps = 0
+        while t < t_end - 1e-14 * max(1.0, abs(t_end)) and steps < max_steps:
+            dt = self.compute_dt()
+            if not (dt > 1e-14 * max(1.0, abs(t_end))) or dt != dt or steps % check_every == check_every - 1:
+                _, code, _ = self.sync(raise_on_error=False)
+                if code or not (dt > 1e-14 * max(1.0, abs(t_end))):
+                    return t, steps, code or ENONPHYS
+            dt = min(dt, t_end - t)
+            self.step(dt)
+            t += dt
+            steps += 1
+        _, code, _ = self.sync(raise_on_error=False)
+        return t, steps, code
+
     def advance(self, n, dt=0.0):
         _check(lib().cgks_advance(self.h, int(n), float(dt)), "cgks_advance")
 

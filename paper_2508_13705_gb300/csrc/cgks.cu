@@ -623,7 +623,7 @@ int cgks_default_params(cgks_params* p, int dim, int order)
     p->weno_eps = 1e-8;
     p->tau_c1 = 0.05;
     p->tau_c2 = 1.0;
-    p->dff_lag = CGKS_DFF_LAG_STAGE;
+    p->dff_lag = CGKS_DFF_LAG_STEP;
     return CGKS_OK;
 }
 

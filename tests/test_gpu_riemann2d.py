@@ -52,13 +52,7 @@ def test_configuration_per_step(name, order):
 def run_to(name, n, order, t_end, precision):
     s = cgks.Solver(2, order, n, n, extent=(0, 1, 0, 1), precision=precision, **HG)
     s.set_state(*config(name, n, order))
-    t, steps = 0.0, 0
-    while t < t_end - 1e-14:
-        dt = min(s.compute_dt(), t_end - t)
-        s.step(dt)
-        t += dt
-        steps += 1
-    _, code, bad = s.sync(raise_on_error=False)
+    t, steps, code = s.run_to(t_end, max_steps=20000)
     out = s.get_state()
     s.close()
     return out, code, steps

@@ -73,12 +73,8 @@ def gpu_run(order, N, st, t_end, extent=(0, 1, 0, 1), gamma=1.4):
     """GPU alone to t_end with the CFL step (the last step clipped)."""
     s = cgks.Solver(1, order, N, extent=extent, gamma=gamma, **HG)
     s.set_state(*st)
-    t = 0.0
-    while t < t_end - 1e-14:
-        dt = min(s.compute_dt(), t_end - t)
-        s.step(dt)
-        t += dt
-    s.sync()
+    t, steps, code = s.run_to(t_end, max_steps=20000)
+    assert code == 0 and t >= t_end - 1e-12, (code, t, steps)
     out = s.get_state()
     s.close()
     return out
