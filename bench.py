@@ -42,14 +42,14 @@ HBM_PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # flux kernel's operations per face Gauss point are these over 2 m (n + 1) / n
 # points per cell.
 KERNEL_COUNTS = {
-    ("fp32", 9): {"s1_lines": (612.8, 24.1, 215.9), "s1_normal": (3638.2, 0.0, 1009.2),
-                  "s1_flux": (19284.8, 0.0, 1319.5), "s1_update": (384.0, 42.0, 930.6),
-                  "s2_lines": (612.8, 24.1, 216.4), "s2_normal": (3638.2, 0.0, 1008.4),
-                  "s2_flux": (18329.9, 0.0, 1015.8), "s2_update": (256.0, 16.0, 625.7)},
-    ("fp64", 9): {"s1_lines": (636.9, 636.9, 447.1), "s1_normal": (3678.3, 3678.3, 2072.2),
-                  "s1_flux": (21492.8, 21492.8, 2761.3), "s1_update": (426.0, 426.0, 1751.8),
-                  "s2_lines": (636.9, 636.9, 447.2), "s2_normal": (3678.3, 3678.3, 2072.9),
-                  "s2_flux": (20275.8, 20275.8, 2192.0), "s2_update": (272.0, 272.0, 1158.0)},
+    ("fp32", 9): {"s1_lines": (612.8, 24.1, 227.5), "s1_normal": (3638.2, 0.0, 1010.4),
+                  "s1_flux": (19284.7, 0.0, 1320.4), "s1_update": (544.0, 58.0, 933.9),
+                  "s2_lines": (612.8, 24.1, 228.0), "s2_normal": (3638.2, 0.0, 1009.6),
+                  "s2_flux": (18329.9, 0.0, 1015.3), "s2_update": (336.0, 24.0, 626.9)},
+    ("fp64", 9): {"s1_lines": (637.6, 637.6, 448.5), "s1_normal": (3679.6, 3679.6, 2092.0),
+                  "s1_flux": (21492.8, 21492.8, 2760.3), "s1_update": (506.0, 506.0, 1752.1),
+                  "s2_lines": (637.6, 637.6, 448.8), "s2_normal": (3679.6, 3679.6, 2088.9),
+                  "s2_flux": (20275.8, 20275.8, 2191.5), "s2_update": (312.0, 312.0, 1158.1)},
 }
 
 
