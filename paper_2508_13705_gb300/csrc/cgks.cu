@@ -62,7 +62,7 @@ int load_tables()
     return CGKS_OK;
 }
 
-Kfns pick_kfns(int dim, int order, int prec, int tau_mode)
+Kfns pick_kfns(int dim, int order, int prec, int tau_mode, const int bc[4])
 {
     int M = (order - 1) / 2;
     Kfns k;
@@ -74,6 +74,10 @@ Kfns pick_kfns(int dim, int order, int prec, int tau_mode)
         for (int c = 0; c < 2; ++c) { k.flux1v[c] = k.flux1h[c]; k.flux2v[c] = k.flux2h[c]; }
     k.flux1 = k.flux1v[0];
     k.flux2 = k.flux2v[0];
+    // stencil kernels with the wall ghost rules only where a side is a wall
+    bool walls = false;
+    for (int s = 0; s < (dim == 2 ? 4 : 2); ++s) walls = walls || bc[s] >= CGKS_BC_REFLECTIVE;
+    if (walls) { k.lines = k.linesw; k.normal = k.normalw; }
     return k;
 }
 
@@ -285,7 +289,7 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return CGKS_ECUDA; }
         b->own_stream = true;
     }
-    b->k = pick_kfns(p->dim, p->order, p->precision, p->tau_mode);
+    b->k = pick_kfns(p->dim, p->order, p->precision, p->tau_mode, p->bc);
     std::vector<Layout> L(n);
     size_t total = 0;
     std::vector<size_t> base(n);
@@ -1027,7 +1031,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     if (sigma_in && sigma_in != sigma_out)
         CK(cudaMemcpyAsync(sigma_out, sigma_in, (size_t)(nx + 1) * 8, cudaMemcpyDeviceToDevice, st));
     if (dt > 0.0) CK(cudaMemcpyAsync(g.dt + 0, &dt, 8, cudaMemcpyHostToDevice, st));
-    Kfns k = pick_kfns(1, p->order, p->precision, p->tau_mode);
+    Kfns k = pick_kfns(1, p->order, p->precision, p->tau_mode, p->bc);
     int nsm = 1;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     auto go = [&](const void* fn, int kind, int stage, bool has_stage, int threads) -> int {

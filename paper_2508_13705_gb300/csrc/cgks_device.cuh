@@ -161,8 +161,11 @@ __device__ __forceinline__ bool wall_flip(int kind, int v, int normal, int bc)
     return rev != dnormal;
 }
 
-// kind: 0 W, 1 Wx, 2 Wy, 3 Wx_line, 4 Wy_line (global orientation)
-template <int D, int M, typename T>
+// kind: 0 W, 1 Wx, 2 Wy, 3 Wx_line, 4 Wy_line (global orientation).
+// WALLS = false compiles the wall branches out: the stencil kernels have a
+// wall-free instance for meshes without walls, whose hot loops the (never
+// taken) wall code would otherwise slow down.
+template <int D, int M, typename T, bool WALLS = true>
 __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, int l, int i, int j)
 {
     bool zero = false, neg = false;
@@ -174,7 +177,7 @@ __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, in
         } else if (bc == BC_FIXED) {
             int layer = side == 0 ? (-1 - i) : (i - g.nx);
             return (T)g.ghost[((side * 3 + layer) * 2 + (kind == 0 ? 0 : 1)) * 3 + v];
-        } else if (is_wall(bc)) {
+        } else if (WALLS && is_wall(bc)) {
             // ghost cell -1-k mirrors cell k; lines across x (Wy_line) swap ends
             i = i < 0 ? -1 - i : 2 * g.nx - 1 - i;
             neg = wall_flip<D>(kind, v, 0, bc);
@@ -188,7 +191,7 @@ __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, in
         int bc = g.bc[j < 0 ? 2 : 3];
         if (bc == BC_PERIODIC) {
             j = imod(j, g.ny);
-        } else if (is_wall(bc)) {
+        } else if (WALLS && is_wall(bc)) {
             j = j < 0 ? -1 - j : 2 * g.ny - 1 - j;
             neg = neg != wall_flip<D>(kind, v, 1, bc);
             if (kind == 3) l = M - 1 - l;
@@ -217,36 +220,37 @@ __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, in
 
 // sigma of x-face f (between cells f-1 and f) in row j; ghost faces: periodic
 // wrap, otherwise 0 beyond the boundary face and the nearest row across y.
-template <int D>
+template <int D, bool WALLS = true>
 __device__ __forceinline__ double sigx(const Mesh& g, const double* sx, int f, int j)
 {
     if (f < 0 || f > g.nx) {
         int bc = g.bc[f < 0 ? 0 : 1];
         if (bc == BC_PERIODIC) f = imod(f, g.nx);
-        else if (is_wall(bc)) f = f < 0 ? -f : 2 * g.nx - f;  // beyond a wall: the mirrored face
+        else if (WALLS && is_wall(bc)) f = f < 0 ? -f : 2 * g.nx - f;  // beyond a wall: the mirrored face
         else return 0.0;
     }
     if (D == 2 && (j < 0 || j >= g.ny)) {
         int bc = g.bc[j < 0 ? 2 : 3];
         if (bc == BC_PERIODIC) j = imod(j, g.ny);
-        else if (is_wall(bc)) j = j < 0 ? -1 - j : 2 * g.ny - 1 - j;
+        else if (WALLS && is_wall(bc)) j = j < 0 ? -1 - j : 2 * g.ny - 1 - j;
         else j = j < 0 ? 0 : g.ny - 1;
     }
     return sx[(long long)j * (g.nx + 1) + f];
 }
 
+template <bool WALLS = true>
 __device__ __forceinline__ double sigy(const Mesh& g, const double* sy, int i, int f)
 {
     if (f < 0 || f > g.ny) {
         int bc = g.bc[f < 0 ? 2 : 3];
         if (bc == BC_PERIODIC) f = imod(f, g.ny);
-        else if (is_wall(bc)) f = f < 0 ? -f : 2 * g.ny - f;
+        else if (WALLS && is_wall(bc)) f = f < 0 ? -f : 2 * g.ny - f;
         else return 0.0;
     }
     if (i < 0 || i >= g.nx) {
         int bc = g.bc[i < 0 ? 0 : 1];
         if (bc == BC_PERIODIC) i = imod(i, g.nx);
-        else if (is_wall(bc)) i = i < 0 ? -1 - i : 2 * g.nx - 1 - i;
+        else if (WALLS && is_wall(bc)) i = i < 0 ? -1 - i : 2 * g.nx - 1 - i;
         else i = i < 0 ? 0 : g.nx - 1;
     }
     return sy[(long long)f * g.nx + i];

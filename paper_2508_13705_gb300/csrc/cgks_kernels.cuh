@@ -35,7 +35,7 @@ __device__ __forceinline__ void local_dims(const Mesh& g, int dir, int& na, int&
 }
 
 // cell value in local coordinates; lkind: 0 W, 1 W_n (cell), 2 W_t (cell), 3 W_n line
-template <int D, int M, typename T>
+template <int D, int M, typename T, bool WALLS = true>
 __device__ __forceinline__ T lcell(const Mesh& g, const T* S, int dir, int lkind, int v, int l, int a, int b)
 {
     int kind;
@@ -44,18 +44,19 @@ __device__ __forceinline__ T lcell(const Mesh& g, const T* S, int dir, int lkind
     else if (lkind == 2) kind = dir == 0 ? 2 : 1;
     else kind = dir == 0 ? 3 : 4;
     int i = dir == 0 ? a : b, j = dir == 0 ? b : a;
-    return cell<D, M, T>(g, S, kind, vglob(dir, v), l, i, j);
+    return cell<D, M, T, WALLS>(g, S, kind, vglob(dir, v), l, i, j);
 }
 
 // sigma of normal faces (f, b) and of tangential faces of column a (a, f)
-template <int D>
+template <int D, bool WALLS = true>
 __device__ __forceinline__ double lsigN(const Mesh& g, const double* sx, const double* sy, int dir, int f, int b)
 {
-    return dir == 0 ? sigx<D>(g, sx, f, b) : sigy(g, sy, b, f);
+    return dir == 0 ? sigx<D, WALLS>(g, sx, f, b) : sigy<WALLS>(g, sy, b, f);
 }
+template <bool WALLS = true>
 __device__ __forceinline__ double lsigT(const Mesh& g, const double* sx, const double* sy, int dir, int a, int f)
 {
-    return dir == 0 ? sigy(g, sy, a, f) : sigx<2>(g, sx, f, a);
+    return dir == 0 ? sigy<WALLS>(g, sy, a, f) : sigx<2, WALLS>(g, sx, f, a);
 }
 
 // Scratch indexing.  Direction 0 keeps the normal index a (= i) fastest,
@@ -96,7 +97,7 @@ __device__ __forceinline__ void flag_bad(const Mesh& g, long long idx)
 }
 
 // -------------------------------------------------------------- Step 1 (2-D)
-template <int M, typename R>
+template <int M, typename R, bool WALLS>
 __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
 {
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
@@ -144,8 +145,8 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
             for (int v = 0; v < 4; ++v)
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
-                    sw[v][q] = lcell<2, M, R>(g, S, dir, 0, v, 0, a, b + q - 2);
-                    swt[v][q] = lcell<2, M, R>(g, S, dir, 2, v, 0, a, b + q - 2);
+                    sw[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 0, v, 0, a, b + q - 2);
+                    swt[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 2, v, 0, a, b + q - 2);
                 }
         }
         // face sigma of the tangential stencil: a direct walk for interior cells
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
             for (int q = 0; q < 6; ++q) s6[q] = sp[q * ss];
         } else {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) s6[q] = lsigT(g, SX, SY, dir, a, b - 2 + q);
+            for (int q = 0; q < 6; ++q) s6[q] = lsigT<WALLS>(g, SX, SY, dir, a, b - 2 + q);
         }
         DffR<R> dff = dff_r<R>(dff_select(g.order, s6, g.thr));
         R ht = (R)(dir == 0 ? g.dy : g.dx);
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
                 for (int q = 0; q < 6; ++q) n6[q] = sp[q * ss];
             } else {
 #pragma unroll
-                for (int q = 0; q < 6; ++q) n6[q] = lsigN<2>(g, SX, SY, dir, a - 2 + q, b);
+                for (int q = 0; q < 6; ++q) n6[q] = lsigN<2, WALLS>(g, SX, SY, dir, a - 2 + q, b);
             }
             R pk[4];
             dff_pack<R>(dff_r<R>(dff_select(g.order, n6, g.thr)), pk);
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
 
 // -------------------------------------------------------------- Step 2
 // D == 1: the cell data are the cell averages and slopes themselves.
-template <int D, int M, typename R>
+template <int D, int M, typename R, bool WALLS>
 __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
 {
     __shared__ unsigned long long cnt[4];
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
             // sigma of the DFF: step n-1, or in stage 2 of the stage-lag reading the
             // face means of stage 1 of this step
             const double* SX = (stage == 2 && g.dff_lag) ? g.sig_xn : g.sig_x;
-            for (int q = 0; q < 6; ++q) s6[q] = sigx<1>(g, SX, a - 2 + q, 0);
+            for (int q = 0; q < 6; ++q) s6[q] = sigx<1, WALLS>(g, SX, a - 2 + q, 0);
             dff = dff_r<R>(dff_select(g.order, s6, g.thr));
         }
         {
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) sl[v][q] = lcell<2, M, R>(g, S, dir, 3, v, l, a + q - 2, b);
+                    for (int q = 0; q < 5; ++q) sl[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 3, v, l, a + q - 2, b);
             }
         }
         const R ghi = (R)g.ghi, glo = (R)g.glo, eps = (R)g.eps;
@@ -314,12 +315,12 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         } else {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                R qi = cell<1, 1, R>(g, S, 0, v, 0, a, 0);
+                R qi = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a, 0);
                 R dp[10];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
-                    dp[q] = cell<1, 1, R>(g, S, 0, v, 0, a + q - 2, 0) - qi;
-                    dp[5 + q] = hn * cell<1, 1, R>(g, S, 1, v, 0, a + q - 2, 0);
+                    dp[q] = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a + q - 2, 0) - qi;
+                    dp[5 + q] = hn * cell<1, 1, R, WALLS>(g, S, 1, v, 0, a + q - 2, 0);
                 }
                 R out[6];
                 recon<R, 6>(dff, g.oi, 0, dp, out, ghi, glo, eps);

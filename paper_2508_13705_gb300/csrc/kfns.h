@@ -7,7 +7,8 @@ namespace cgks {
 typedef void (*KStage)(Work, int);
 typedef void (*KOne)(Work);
 struct Kfns {
-    KStage lines, normal;
+    KStage lines, normal;      // instances for meshes without walls
+    KStage linesw, normalw;    // the same with the wall ghost rules
     KOne flux1, flux2, upd1, upd2, cfl, siginit, check;
     KStage convert;  // FP32-bulk state copies (to_float = 1: FP64 -> float planes)
     KOne flux1v[2], flux2v[2];  // flux variants: [0] uncapped, [1] register-capped (tau = 0)

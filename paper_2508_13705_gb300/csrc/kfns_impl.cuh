@@ -17,8 +17,10 @@ template <int D, int M, typename R>
 Kfns make_kfns()
 {
     Kfns k;
-    k.lines = D == 2 ? (KStage)k_lines<M, R> : nullptr;
-    k.normal = k_normal<D, M, R>;
+    k.lines = D == 2 ? (KStage)k_lines<M, R, false> : nullptr;
+    k.normal = k_normal<D, M, R, false>;
+    k.linesw = D == 2 ? (KStage)k_lines<M, R, true> : nullptr;
+    k.normalw = k_normal<D, M, R, true>;
     k.flux1v[0] = k_flux<D, M, R, 1, 0, 0>;
     k.flux2v[0] = k_flux<D, M, R, 2, 0, 0>;
     k.flux1v[1] = k_flux<D, M, R, 1, 1, 0>;
