@@ -179,12 +179,23 @@ class Solver:
         arr, p = _host(ghost, (36,))
         _check(lib().cgks_set_ghost(self.h, p), "cgks_set_ghost")
 
-    def get_state(self):
+    def get_state(self, out=None):
+        """Copy the state to the host as FP64 arrays (dict keyed W, Wx, ...).
+        ``out``: optional dict of caller-owned C-contiguous float64 arrays of
+        the right sizes (pinned ones give the fastest copies), filled in place
+        and returned."""
         sh = self._shapes()
         names = ["W", "Wx", "Wy", "Wx_line", "Wy_line", "sigma_x", "sigma_y"]
         if self.dim == 1:
             names = ["W", "Wx", "sigma_x"]
-        out = {n: np.zeros(sh[n]) for n in names}
+        if out is None:
+            out = {n: np.zeros(sh[n]) for n in names}
+        else:
+            for n in names:
+                a = out[n]
+                if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                        and a.size == int(np.prod(sh[n]))):
+                    raise ValueError("out[%r] must be a C-contiguous float64 array of %s values" % (n, sh[n]))
         ptr = lambda n: out[n].ctypes.data_as(ctypes.c_void_p) if n in out else None
         _check(lib().cgks_get_state(self.h, *[ptr(n) for n in ("W", "Wx", "Wy", "Wx_line", "Wy_line",
                                                                  "sigma_x", "sigma_y")]), "cgks_get_state")

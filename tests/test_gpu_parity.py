@@ -357,3 +357,22 @@ def test_autotune_keeps_results_bitwise_and_state():
     assert outs[0][0] == outs[1][0]
     for f in FIELDS_2D:
         assert np.array_equal(outs[0][1][f], outs[1][1][f]), f
+
+
+def test_get_state_into_caller_buffers():
+    """get_state(out=...) fills caller-owned (here pinned) arrays in place with
+    the same values as a fresh copy."""
+    import torch
+    n = 16
+    st = inputs.quadrants_2d(n, 7, seed=1)
+    s = cgks.Solver(2, 7, n, n, extent=(0, 1, 0, 1), tau_mode=cgks.TAU_HGKS, bc=(1, 1, 1, 1))
+    s.set_state(*st)
+    s.advance(2, 0.0)
+    s.sync()
+    a = s.get_state()
+    out = {k: torch.zeros(v.shape, dtype=torch.float64).pin_memory().numpy() for k, v in a.items()}
+    b = s.get_state(out=out)
+    assert b is out
+    for k in a:
+        assert np.array_equal(a[k], out[k]), k
+    s.close()
