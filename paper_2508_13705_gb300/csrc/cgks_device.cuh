@@ -432,10 +432,6 @@ __device__ __forceinline__ void recon(const DffR<R>& dff, int oi, int row0, cons
     recon_ao<R, NOUT>(dff.a, oi, row0, dp, out, ghi, glo, eps);
 }
 
-// The same with the order (table index OI) and the first output row fixed at
-// compile time, for the 2-D kernels, whose instantiation fixes the order: each
-// linear branch then takes its stencil row from a constant address, so the
-// coefficients enter the FMAs as constant-bank operands instead of loads.
 // The taps of dp = (Qbar_{i-2..i+2} - Qbar_i, h Qx_{i-2..i+2}) that a linear
 // stencil of Sec. 3.2 uses: the own average enters only through the
 // differences (dp[2] = 0) and the own gradient not at all; r5 spans cells
@@ -449,6 +445,10 @@ __host__ __device__ constexpr bool st_tap(int st, int k)
          : true;
 }
 
+// A linear stencil with the order (table index OI), the stencil and the first
+// output row fixed at compile time, for the 2-D kernels, whose instantiation
+// fixes the order: the stencil row comes from a constant address, so the
+// coefficients enter the FMAs as constant-bank operands instead of loads.
 template <typename R, int NOUT, int OI, int ST, int ROW0>
 __device__ __forceinline__ void recon_lin(const R dp[10], R out[NOUT])
 {
@@ -462,6 +462,7 @@ __device__ __forceinline__ void recon_lin(const R dp[10], R out[NOUT])
         out[r] = s;
     }
 }
+
 // Compile-time stencil tag (-1: HWENO-AO) for branch-hoisted reconstruction
 // loops: the branch on a cell's stencil is taken once, outside the loop over
 // variables, so each branch is one straight run of code.
@@ -486,14 +487,6 @@ __device__ __forceinline__ void with_stencil(const DffR<R>& dff, Body&& body)
     else body(StTag<-1>());
 }
 
-template <typename R, int NOUT, int OI, int ROW0>
-__device__ __forceinline__ void recon_k(const DffR<R>& dff, const R dp[10], R out[NOUT], R ghi, R glo, R eps)
-{
-    if (OI == 2 && dff.st == ST_R9) recon_lin<R, NOUT, OI, ST_R9, ROW0>(dp, out);
-    else if (OI >= 1 && dff.st == ST_R7) recon_lin<R, NOUT, OI, ST_R7, ROW0>(dp, out);
-    else if (dff.st == ST_R5) recon_lin<R, NOUT, OI, ST_R5, ROW0>(dp, out);
-    else recon_ao<R, NOUT>(dff.a, OI, ROW0, dp, out, ghi, glo, eps);
-}
 
 // ------------------------------------------------------------------ kinetics
 
