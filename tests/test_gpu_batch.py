@@ -28,13 +28,19 @@ def ext_of(sp):
     return (0.0, 1.0, 0.0, sp["ny"] / sp["nx"])
 
 
-@pytest.mark.parametrize("precision", [cgks.FP64, cgks.FP32_BULK])
-def test_batch_equals_single_instances_bitwise(precision):
+@pytest.mark.parametrize("precision,kw", [
+    (cgks.FP64, {}), (cgks.FP32_BULK, {}),
+    # slip walls and the viscous collision time: the wall instances of the
+    # stencil kernels and the viscous flux inside the batch graph
+    (cgks.FP64, dict(bc=(cgks.BC_REFLECTIVE, cgks.BC_REFLECTIVE, cgks.BC_NOSLIP, cgks.BC_NOSLIP),
+                     tau_mode=cgks.TAU_NS, mu=1e-3))])
+def test_batch_equals_single_instances_bitwise(precision, kw):
     sp = specs()
     order = 7
     states = [inputs.batch_instance(s, order) for s in sp]
+    kw = dict(dict(tau_mode=cgks.TAU_HGKS), **kw)
     b = cgks.Batch(order, [s["nx"] for s in sp], [s["ny"] for s in sp], [ext_of(s) for s in sp],
-                   precision=precision, tau_mode=cgks.TAU_HGKS)
+                   precision=precision, **kw)
     for k, st in enumerate(states):
         b.set_state(k, *st)
     dts = np.array([2e-4 * (1 + 0.1 * k) for k in range(len(sp))])
@@ -43,8 +49,7 @@ def test_batch_equals_single_instances_bitwise(precision):
     b.step(None)  # a CFL step: every instance takes its own time step
     b.sync()
     for k, (s, st) in enumerate(zip(sp, states)):
-        one = cgks.Solver(2, order, s["nx"], s["ny"], extent=ext_of(s), precision=precision,
-                          tau_mode=cgks.TAU_HGKS)
+        one = cgks.Solver(2, order, s["nx"], s["ny"], extent=ext_of(s), precision=precision, **kw)
         one.set_state(*st)
         for _ in range(3):
             one.step(dts[k])
