@@ -78,6 +78,27 @@ extern "C" {
                                    normal momentum reversed); ghost faces mirror sigma */
 #define CGKS_BC_NOSLIP 4        /* adiabatic no-slip wall (Sec. 4.9): the same mirror with
                                    both momentum components reversed */
+#define CGKS_BC_INFLOW 5        /* 2-D: ghost cells hold a prescribed state with zero slopes
+                                   (the supersonic inflow and the exact shock motion of
+                                   Sec. 4.8): bc_state[side][0] where the ghost cell's centre
+                                   coordinate along the side (y on x-sides, x on y-sides)
+                                   lies below split(t) = bc_split[side][0] + bc_split[side][1] t,
+                                   bc_state[side][1] elsewhere, t the stage's time (t^n in
+                                   stage 1, t^n + dt/2 in stage 2); beyond the side sigma is 0
+                                   at the faces parallel to it and copies the nearest row or
+                                   column along it, as at a transmissive side */
+#define CGKS_BC_INFLOW_REFLECTIVE 6 /* 2-D: bc_state[side][0] below split(t), a slip wall
+                                   beyond it (the bottom of Sec. 4.8); sigma mirrors as at
+                                   a wall along the whole side */
+/* first-order fallback at face Gauss points (not a step of the paper, which
+   states no limiter; off by default) */
+#define CGKS_PT_FALLBACK_OFF 0
+#define CGKS_PT_FALLBACK_FIRST_ORDER 1 /* a side of a face Gauss point whose reconstructed
+                                   state has rho <= 0 or p <= 0 (tested in the bulk
+                                   precision) takes the average of the cell it was
+                                   reconstructed from, with every derivative zero; sigma
+                                   then comes from the states used; counted in
+                                   cgks_stats.fallbacks */
 
 typedef struct {
     int dim;            /* 1 or 2 */
@@ -95,6 +116,10 @@ typedef struct {
     double tau_c2;      /* c2 of the HGKS collision time (1.0) */
     double mu;          /* dynamic viscosity of CGKS_TAU_NS (constant), >= 0 */
     int dff_lag;        /* CGKS_DFF_LAG_STEP (default) or CGKS_DFF_LAG_STAGE */
+    int pt_fallback;    /* CGKS_PT_FALLBACK_OFF (default) or CGKS_PT_FALLBACK_FIRST_ORDER */
+    double bc_state[4][2][4]; /* prescribed ghost states of CGKS_BC_INFLOW* sides, conservative
+                                 (rho, rho U, rho V, rho E), rho > 0 and p > 0 */
+    double bc_split[4][2];    /* split point along each such side: [0] + [1] t */
 } cgks_params;
 
 typedef struct cgks_solver cgks_solver;
@@ -108,11 +133,14 @@ typedef struct {
     long long branch[4]; /* normal-reconstruction branches (per cell and Gauss
                             line, both directions) of the latest step's two
                             stages: HWENO-AO, linear r5, r7, r9 (batches: summed) */
+    long long fallbacks; /* face-point sides that took CGKS_PT_FALLBACK_FIRST_ORDER since
+                            the last set_state (both stages and directions) */
 } cgks_stats;
 
 /* Fill *p with the paper's defaults for (dim, order): gamma 1.4, CFL 0.5,
  * sigma_thres 1, gamma_hi 0.85, gamma_lo 0.6, eps 1e-8, c1 0.05, c2 1, mu 0,
- * FP64, tau = 0, periodic, step-lag DFF.  Returns CGKS_EINVAL for a NULL p. */
+ * FP64, tau = 0, periodic, step-lag DFF, no point fallback, zero inflow
+ * states.  Returns CGKS_EINVAL for a NULL p. */
 int cgks_default_params(cgks_params* p, int dim, int order);
 
 /* Create a solver for an nx x ny mesh on [x0,x1] x [y0,y1] (1-D: ny = 1,
@@ -120,16 +148,20 @@ int cgks_default_params(cgks_params* p, int dim, int order);
  * device; the CUDA graph of one step is captured on first use.
  * Errors: CGKS_EINVAL (NULL out/p, dim not 1/2, order not 5/7/9, nx or ny < 1,
  * ny != 1 in 1-D, gamma <= 1, cfl <= 0, non-positive extent, FIXED bc in 2-D,
+ * INFLOW bc in 1-D, an inflow side whose states are not physical or whose
+ * split is not finite, a wall or inflow side across fewer than 3 cells,
+ * pt_fallback not 0/1,
  * a mesh with 2^31 or more face Gauss points: about 16000^2 cells at order 9,
  * more than the device memory holds), CGKS_ENOMEM, CGKS_ECUDA.  On error *out
  * is NULL. */
 int cgks_init_mesh(cgks_solver** out, const cgks_params* p, int nx, int ny,
                    double x0, double x1, double y0, double y1, void* stream);
 
-/* Copy a host state in (synchronous).  sigma_x / sigma_y may be NULL: sigma is
- * then initialised from Eq. 3.2 applied to the two cell averages adjacent to
- * each face.  Returns CGKS_ENONPHYS if some cell has rho <= 0 or p <= 0,
- * CGKS_EINVAL for a NULL required array. */
+/* Copy a host state in (synchronous); the simulated time and the fallback
+ * count restart from 0.  sigma_x / sigma_y may be NULL: sigma is then
+ * initialised from Eq. 3.2 applied to the two cell averages adjacent to each
+ * face (ghost cells of inflow sides taken at t = 0).  Returns CGKS_ENONPHYS if
+ * some cell has rho <= 0 or p <= 0, CGKS_EINVAL for a NULL required array. */
 int cgks_set_state(cgks_solver* s, const double* W, const double* Wx, const double* Wy,
                    const double* Wx_line, const double* Wy_line,
                    const double* sigma_x, const double* sigma_y);
@@ -139,6 +171,11 @@ int cgks_set_state(cgks_solver* s, const double* W, const double* Wx, const doub
 int cgks_set_state_device(cgks_solver* s, const double* W, const double* Wx, const double* Wy,
                           const double* Wx_line, const double* Wy_line,
                           const double* sigma_x, const double* sigma_y);
+
+/* Set the simulated time (the t^n of the next step), e.g. to resume a run or
+ * to place the split points of inflow sides; enqueued on the solver's stream.
+ * CGKS_EINVAL for a NULL solver or a non-finite t. */
+int cgks_set_time(cgks_solver* s, double t);
 
 /* 1-D, CGKS_BC_FIXED sides: ghost cells [2 sides][3 layers][2 fields W,Wx][3 vars]
  * (layer 0 touches the boundary).  Host pointer; copied. */

@@ -38,6 +38,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
 
 BC_PERIODIC, BC_TRANSMISSIVE, BC_FIXED, BC_REFLECTIVE, BC_NOSLIP = 0, 1, 2, 3, 4
+BC_INFLOW, BC_INFLOW_REFLECTIVE = 5, 6
 TAU_ZERO, TAU_HGKS, TAU_NS = 0, 1, 2
 DFF_LAG_STEP, DFF_LAG_STAGE = 0, 1
 
@@ -63,7 +64,9 @@ class OParams(ctypes.Structure):
                 ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("gamma", ctypes.c_double),
                 ("sigma_thres", ctypes.c_double), ("gamma_hi", ctypes.c_double),
                 ("gamma_lo", ctypes.c_double), ("weno_eps", ctypes.c_double),
-                ("c1", ctypes.c_double), ("c2", ctypes.c_double), ("mu", ctypes.c_double)]
+                ("c1", ctypes.c_double), ("c2", ctypes.c_double), ("mu", ctypes.c_double),
+                ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("tb", ctypes.c_double),
+                ("bcs", ctypes.c_double * 32), ("bcx", ctypes.c_double * 8), ("pt_fallback", ctypes.c_int)]
 
 
 _lib = None
@@ -75,10 +78,10 @@ def lib():
         _lib = ctypes.CDLL(build())
         dp = ctypes.POINTER(ctypes.c_double)
         P = ctypes.POINTER(OParams)
-        _lib.oracle_faces_1d.argtypes = [P, dp, dp, dp, dp, dp, ctypes.c_double, dp, dp,
-                                         ctypes.POINTER(ctypes.c_int)]
+        ip = ctypes.POINTER(ctypes.c_int)
+        _lib.oracle_faces_1d.argtypes = [P, dp, dp, dp, dp, dp, ctypes.c_double, dp, dp, ip, ip]
         _lib.oracle_faces_2d.argtypes = [P, dp, dp, ctypes.c_int, dp, dp, dp, dp, dp, dp, dp,
-                                         ctypes.c_double, dp, dp]
+                                         ctypes.c_double, dp, dp, ip]
         for f in ("oracle_point_1d", "oracle_point_2d"):
             getattr(_lib, f).argtypes = [P, dp, dp, ctypes.c_double, dp]
         _lib.oracle_moments.argtypes = [P, dp, dp, dp, dp]
@@ -108,8 +111,10 @@ class Oracle:
 
     def __init__(self, dim, order, nx, ny=1, extent=(0.0, 1.0, 0.0, 1.0), gamma=1.4, cfl=0.5,
                  tau_mode=TAU_ZERO, bc=(BC_PERIODIC,) * 4, sigma_thres=1.0, gamma_hi=0.85,
-                 gamma_lo=0.6, weno_eps=1e-8, c1=0.05, c2=1.0, step3=0, mu=0.0, dff_lag=DFF_LAG_STEP):
+                 gamma_lo=0.6, weno_eps=1e-8, c1=0.05, c2=1.0, step3=0, mu=0.0, dff_lag=DFF_LAG_STEP,
+                 bc_state=None, bc_split=None, pt_fallback=0):
         assert dim in (1, 2) and order in (5, 7, 9)
+        assert dim == 2 or not any(b in (BC_INFLOW, BC_INFLOW_REFLECTIVE) for b in bc)
         self.dim, self.order, self.nx, self.ny = dim, order, nx, (ny if dim == 2 else 1)
         self.nv = dim + 2
         self.m = gauss_points(order) if dim == 2 else 1
@@ -129,6 +134,19 @@ class Oracle:
         P.sigma_thres, P.gamma_hi, P.gamma_lo = sigma_thres, gamma_hi, gamma_lo
         P.weno_eps, P.c1, P.c2 = weno_eps, c1, c2
         P.mu = mu
+        # inflow sides: ghost cells hold bc_state[side][0] where the centre
+        # coordinate along the side is below bc_split[side][0] + bc_split[side][1] t,
+        # bc_state[side][1] beyond (conservative variables)
+        self.x0, self.y0 = x0, y0
+        self.bc_state = np.zeros((4, 2, 4)) if bc_state is None else np.asarray(bc_state, dtype=np.float64).reshape(4, 2, 4)
+        self.bc_split = np.zeros((4, 2)) if bc_split is None else np.asarray(bc_split, dtype=np.float64).reshape(4, 2)
+        P.x0, P.y0 = x0, y0
+        P.bcs[:] = self.bc_state.ravel().tolist()
+        P.bcx[:] = self.bc_split.ravel().tolist()
+        # flagged option (the paper states no limiter): a face point side whose
+        # reconstructed state is not physical falls back to its cell's average
+        P.pt_fallback = pt_fallback
+        self.fallbacks = 0
         self.mu, self.tau_mode = mu, tau_mode
         # reading of the DFF time lag (Sec. 3.1): sigma of stage 1 of step n-1
         # in both stages of step n (STEP), or in stage 2 the sigma of stage 1 of
@@ -154,6 +172,7 @@ class Oracle:
             self.ghost = np.ascontiguousarray(ghost, dtype=np.float64).reshape(2, 3, 2, 3).copy()
         if self.dim == 1:
             self.Wy = self.Wxl = self.Wyl = None
+        self.fallbacks = 0
         if sigma_x is None:
             sigma_x, sigma_y = self.initial_sigma()
         self.sx = c(sigma_x)
@@ -182,12 +201,27 @@ class Oracle:
                     q[v] = -q[v]
             return q
 
+        def prescribed(side, wall):
+            # centres along the side against its split point at the current time
+            if axis == 0:
+                s = self.y0 + (np.arange(self.ny) + 0.5) * self.dy
+                s = s.reshape(1, -1, 1)
+            else:
+                s = self.x0 + (np.arange(self.nx) + 0.5) * self.dx
+                s = s.reshape(1, 1, -1)
+            below = s < self.bc_split[side, 0] + self.bc_split[side, 1] * self.t
+            a = self.bc_state[side, 0].reshape(-1, 1, 1)
+            b = wall if wall is not None else self.bc_state[side, 1].reshape(-1, 1, 1)
+            return np.where(below, a, b)
+
         if lo_bc == BC_PERIODIC:
             lo = take(n - 1)
         elif lo_bc == BC_FIXED:
             lo = self.ghost[0, 0, 0].reshape(-1, 1, 1)
         elif lo_bc in (BC_REFLECTIVE, BC_NOSLIP):
             lo = mirror(take(0), lo_bc)
+        elif lo_bc in (BC_INFLOW, BC_INFLOW_REFLECTIVE):
+            lo = prescribed(2 * axis, mirror(take(0), lo_bc) if lo_bc == BC_INFLOW_REFLECTIVE else None)
         else:
             lo = take(0)
         if hi_bc == BC_PERIODIC:
@@ -196,6 +230,8 @@ class Oracle:
             hi = self.ghost[1, 0, 0].reshape(-1, 1, 1)
         elif hi_bc in (BC_REFLECTIVE, BC_NOSLIP):
             hi = mirror(take(n - 1), hi_bc)
+        elif hi_bc in (BC_INFLOW, BC_INFLOW_REFLECTIVE):
+            hi = prescribed(2 * axis + 1, mirror(take(n - 1), hi_bc) if hi_bc == BC_INFLOW_REFLECTIVE else None)
         else:
             hi = take(n - 1)
         ext = np.concatenate([lo, W, hi], axis=2 - axis)
@@ -260,10 +296,12 @@ class Oracle:
             sig = np.zeros(nx + 1)
             br = np.zeros(nx + 2, dtype=np.int32)
             gh = self.ghost if self.ghost is not None else np.zeros((2, 3, 2, 3))
+            nf = ctypes.c_int(0)
             fl = L.oracle_faces_1d(ctypes.byref(self.P), _p(self.T), _p(W), _p(Wx), _p(self.sx),
                                    _p(np.ascontiguousarray(gh)), dt, _p(out), _p(sig),
-                                   br.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+                                   br.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), ctypes.byref(nf))
             self.flags |= fl
+            self.fallbacks += nf.value
             self.branch = br
             return out.reshape(5, 3, 1, nx + 1), sig
         ox = np.zeros((5, 4, ny, nx + 1, m))
@@ -271,8 +309,11 @@ class Oracle:
         oy = np.zeros((5, 4, ny + 1, nx, m))
         sgy = np.zeros((ny + 1, nx, m))
         args = (_p(W), _p(Wx), _p(Wy), _p(Wxl), _p(Wyl), _p(self.sx), _p(self.sy), dt)
-        self.flags |= L.oracle_faces_2d(ctypes.byref(self.P), _p(self.T), _p(self.gx), 0, *args, _p(ox), _p(sgx))
-        self.flags |= L.oracle_faces_2d(ctypes.byref(self.P), _p(self.T), _p(self.gx), 1, *args, _p(oy), _p(sgy))
+        for d, (o, sg) in enumerate(((ox, sgx), (oy, sgy))):
+            nf = ctypes.c_int(0)
+            self.flags |= L.oracle_faces_2d(ctypes.byref(self.P), _p(self.T), _p(self.gx), d, *args, _p(o), _p(sg),
+                                            ctypes.byref(nf))
+            self.fallbacks += nf.value
         return ox, sgx, oy, sgy
 
     # Gauss-weighted face differences of a face quantity q
@@ -300,6 +341,7 @@ class Oracle:
         dx, dy = self.dx, self.dy
         W, Wx, Wy, Wxl, Wyl = self.W, self.Wx, self.Wy, self.Wxl, self.Wyl
         # ---- stage 1 at t^n
+        self.P.tb = self.t
         r1 = self.faces(dt)
         ox = r1[0]
         Fd, Fh, W0, Wh, Wd = ox
@@ -332,6 +374,7 @@ class Oracle:
             self.sx = np.ascontiguousarray(sig_x_new)
             if self.dim == 2:
                 self.sy = np.ascontiguousarray(sig_y_new)
+        self.P.tb = self.t + 0.5 * dt
         r2 = self.faces(dt, state=(np.ascontiguousarray(Ws), np.ascontiguousarray(Wxs),
                                    None if Wys is None else np.ascontiguousarray(Wys), Wxls, Wyls))
         Fd2, Fh2, W02, Wh2, Wd2 = r2[0]

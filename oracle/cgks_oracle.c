@@ -22,7 +22,8 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_FIXED = 2, BC_REFLECTIVE = 3, BC_NOSLIP = 4 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_FIXED = 2, BC_REFLECTIVE = 3, BC_NOSLIP = 4,
+       BC_INFLOW = 5, BC_INFLOW_REFLECTIVE = 6 };
 enum { K_W = 0, K_WX = 1, K_WY = 2, K_WXL = 3, K_WYL = 4 };
 enum { ST_S0 = 0, ST_S1 = 1, ST_S2 = 2, ST_R5 = 3, ST_R7 = 4, ST_R9 = 5 };
 /* flag bits */
@@ -41,6 +42,13 @@ typedef struct {
     double dx, dy, gamma;
     double sigma_thres, gamma_hi, gamma_lo, weno_eps, c1, c2;
     double mu;       /* dynamic viscosity (tau_mode 2) */
+    double x0, y0;   /* lower-left corner of the mesh */
+    double tb;       /* time at which prescribed ghost states are taken (this stage's) */
+    /* prescribed ghost states (conservative) per side: [0] where the
+     * coordinate along the side is below split(t) = bcx[0] + bcx[1] t, [1] beyond */
+    double bcs[4][2][4];
+    double bcx[4][2];
+    int pt_fallback; /* 1: first-order fallback at non-physical face points (a flagged option) */
 } OParams;
 
 typedef struct {
@@ -59,9 +67,10 @@ static int imod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
 /* Boundary handling: ghost cells and ghost faces                      */
 /* ------------------------------------------------------------------ */
 
-/* Cell field value with the ghost-cell rule applied direction by direction:
- * periodic wraps; transmissive copies the nearest interior cell and zeroes
- * the slopes normal to that boundary; fixed (1-D) reads the stored ghost. */
+/* Cell field value with the ghost-cell rule applied direction by direction
+ * (x first): periodic wraps; transmissive copies the nearest interior cell and
+ * zeroes the slopes normal to that boundary; fixed (1-D) reads the stored
+ * ghost; a wall mirrors; inflow holds a prescribed state with zero slopes. */
 static int is_wall(int bc) { return bc == BC_REFLECTIVE || bc == BC_NOSLIP; }
 
 /* Sign of a mirrored ghost value across a wall whose normal is the x axis
@@ -74,6 +83,17 @@ static double wall_sign(int kind, int v, int normal, int bc, int nv)
     int rev = (v == 1 + normal) || (bc == BC_NOSLIP && v >= 1 && v <= nv - 2);
     int dnormal = normal == 0 ? (kind == K_WX || kind == K_WXL) : (kind == K_WY || kind == K_WYL);
     return (rev ^ dnormal) ? -1.0 : 1.0;
+}
+
+/* Prescribed ghost states (inflow sides): is the centre of ghost row or
+ * column k, taken along side `side`, below that side's split point at the
+ * stage time, split(t) = bcx[0] + bcx[1] t?  Below it the ghost cell holds
+ * bcs[side][0], beyond it bcs[side][1] (or, on a side that is a slip wall in
+ * part, the mirror image). */
+static int below_split(const OParams *P, int side, int k)
+{
+    double s = side < 2 ? P->y0 + (k + 0.5) * P->dy : P->x0 + (k + 0.5) * P->dx;
+    return s < P->bcx[side][0] + P->bcx[side][1] * P->tb;
 }
 
 static double cellval(const Ctx *c, int kind, int v, int l, int i, int j)
@@ -90,7 +110,10 @@ static double cellval(const Ctx *c, int kind, int v, int l, int i, int j)
             int layer = side == 0 ? (-1 - i) : (i - nx);
             int f = kind == K_W ? 0 : 1;
             return c->ghost[((side * 3 + layer) * 2 + f) * 3 + v];
-        } else if (is_wall(bc)) {
+        } else if (bc == BC_INFLOW || (bc == BC_INFLOW_REFLECTIVE && below_split(P, side, j))) {
+            /* prescribed state by the row's centre, zero slopes */
+            return kind == K_W ? P->bcs[side][below_split(P, side, j) ? 0 : 1][v] : 0.0;
+        } else if (is_wall(bc) || bc == BC_INFLOW_REFLECTIVE) {
             /* ghost cell -1-k mirrors cell k; lines across x (Wy_line) swap ends */
             i = i < 0 ? -1 - i : 2 * nx - 1 - i;
             sgn *= wall_sign(kind, v, 0, bc, c->nv);
@@ -101,10 +124,14 @@ static double cellval(const Ctx *c, int kind, int v, int l, int i, int j)
         }
     }
     if (j < 0 || j >= ny) {
-        int bc = P->bc[j < 0 ? 2 : 3];
+        int side = j < 0 ? 2 : 3;
+        int bc = P->bc[side];
+        if (bc == BC_INFLOW || (bc == BC_INFLOW_REFLECTIVE && below_split(P, side, i)))
+            /* prescribed state by the column's centre (after the x rule), zero slopes */
+            return kind == K_W ? sgn * P->bcs[side][below_split(P, side, i) ? 0 : 1][v] : 0.0;
         if (bc == BC_PERIODIC) {
             j = imod(j, ny);
-        } else if (is_wall(bc)) {
+        } else if (is_wall(bc) || bc == BC_INFLOW_REFLECTIVE) {
             j = j < 0 ? -1 - j : 2 * ny - 1 - j;
             sgn *= wall_sign(kind, v, 1, bc, c->nv);
             if (kind == K_WXL) l = P->m - 1 - l;
@@ -126,7 +153,9 @@ static double cellval(const Ctx *c, int kind, int v, int l, int i, int j)
     }
     return sgn * val;
 }
-/* Face sigma beyond a wall mirrors the interior face (face 0 is the wall). */
+/* Face sigma beyond a wall (or a side that is a wall in part) mirrors the
+ * interior face (face 0 is the wall); beyond other sides it is 0 at the faces
+ * normal to the side and copies the nearest row or column along it. */
 static double sigx(const Ctx *c, int f, int j)
 {
     const OParams *P = c->P;
@@ -134,13 +163,13 @@ static double sigx(const Ctx *c, int f, int j)
     if (f < 0 || f > nx) {
         int bc = P->bc[f < 0 ? 0 : 1];
         if (bc == BC_PERIODIC) f = imod(f, nx);
-        else if (is_wall(bc)) f = f < 0 ? -f : 2 * nx - f;
+        else if (is_wall(bc) || bc == BC_INFLOW_REFLECTIVE) f = f < 0 ? -f : 2 * nx - f;
         else return 0.0;
     }
     if (j < 0 || j >= ny) {
         int bc = P->bc[j < 0 ? 2 : 3];
         if (bc == BC_PERIODIC) j = imod(j, ny);
-        else if (is_wall(bc)) j = j < 0 ? -1 - j : 2 * ny - 1 - j;
+        else if (is_wall(bc) || bc == BC_INFLOW_REFLECTIVE) j = j < 0 ? -1 - j : 2 * ny - 1 - j;
         else j = j < 0 ? 0 : ny - 1;
     }
     return c->sx[(size_t)j * (nx + 1) + f];
@@ -152,13 +181,13 @@ static double sigy(const Ctx *c, int i, int g)
     if (g < 0 || g > ny) {
         int bc = P->bc[g < 0 ? 2 : 3];
         if (bc == BC_PERIODIC) g = imod(g, ny);
-        else if (is_wall(bc)) g = g < 0 ? -g : 2 * ny - g;
+        else if (is_wall(bc) || bc == BC_INFLOW_REFLECTIVE) g = g < 0 ? -g : 2 * ny - g;
         else return 0.0;
     }
     if (i < 0 || i >= nx) {
         int bc = P->bc[i < 0 ? 0 : 1];
         if (bc == BC_PERIODIC) i = imod(i, nx);
-        else if (is_wall(bc)) i = i < 0 ? -1 - i : 2 * nx - 1 - i;
+        else if (is_wall(bc) || bc == BC_INFLOW_REFLECTIVE) i = i < 0 ? -1 - i : 2 * nx - 1 - i;
         else i = i < 0 ? 0 : nx - 1;
     }
     return c->sy[(size_t)g * nx + i];
@@ -679,6 +708,24 @@ static void ctx_init(Ctx *c, const OParams *P, const double *T, const double *gx
     c->K = P->dim == 2 ? (4.0 - 2.0 * P->gamma) / (P->gamma - 1.0) : (3.0 - P->gamma) / (P->gamma - 1.0);
 }
 
+/* First-order fallback at a face point (a flagged option; the paper states
+ * no limiter): a side whose reconstructed state has rho <= 0 or p <= 0 takes
+ * avg, the average of the cell it was reconstructed from, with every
+ * derivative zero.  Returns 1 when it applied. */
+static int point_fallback(const Ctx *c, Side *S, const double *avg)
+{
+    int nv = c->nv;
+    const double *q = S->D[0];
+    double m2 = q[1] * q[1] + (nv == 4 ? q[2] * q[2] : 0.0);
+    double p = (c->P->gamma - 1.0) * (q[nv - 1] - 0.5 * m2 / q[0]);
+    if (q[0] > 0.0 && p > 0.0) return 0;
+    for (int v = 0; v < nv; v++) {
+        S->D[0][v] = avg[v];
+        for (int k = 1; k < 6; k++) S->D[k][v] = 0.0;
+    }
+    return 1;
+}
+
 /* Build an ASE-DFF polynomial from a 1-D line of data. */
 static int line_poly(const Ctx *c, const double q[5], const double qx[5], double h, const double sig[6], double P[9])
 {
@@ -690,7 +737,7 @@ static int line_poly(const Ctx *c, const double q[5], const double qx[5], double
 /* 1-D faces.  out: [5][3][nx+1]; sig: [nx+1]; branch: [nx+2] (cells -1..nx) */
 int oracle_faces_1d(const OParams *P, const double *T, const double *W, const double *Wx,
                     const double *sx, const double *ghost, double dt,
-                    double *out, double *sig, int *branch)
+                    double *out, double *sig, int *branch, int *nfall)
 {
     Ctx c;
     ctx_init(&c, P, T, NULL, W, Wx, NULL, NULL, NULL, sx, NULL, ghost);
@@ -712,7 +759,8 @@ int oracle_faces_1d(const OParams *P, const double *T, const double *W, const do
             }
         }
     }
-#pragma omp parallel for reduction(| : bad) schedule(static)
+    int nf_total = 0;
+#pragma omp parallel for reduction(| : bad) reduction(+ : nf_total) schedule(static)
     for (int f = 0; f <= nx; f++) {
         Side L, R;
         memset(&L, 0, sizeof L); memset(&R, 0, sizeof R);
@@ -722,6 +770,11 @@ int oracle_faces_1d(const OParams *P, const double *T, const double *W, const do
                 L.D[nd][v] = fl[(((size_t)(cl + 1) * 2 + 0) * 3 + nd) * 4 + v];
                 R.D[nd][v] = fl[(((size_t)(cr + 1) * 2 + 1) * 3 + nd) * 4 + v];
             }
+        if (P->pt_fallback) {
+            double al[3], ar[3];
+            for (int v = 0; v < nv; v++) { al[v] = cellval(&c, K_W, v, 0, cl, 0); ar[v] = cellval(&c, K_W, v, 0, cr, 0); }
+            nf_total += point_fallback(&c, &L, al) + point_fallback(&c, &R, ar);
+        }
         double o[5][4];
         if (!kinetic_point(&c, &L, &R, dt, o)) bad = 1;
         for (int k = 0; k < 5; k++)
@@ -729,6 +782,7 @@ int oracle_faces_1d(const OParams *P, const double *T, const double *W, const do
         sig[f] = sigma_point(&c, L.D[0], R.D[0]);
     }
     free(fl);
+    if (nfall) *nfall = nf_total;
     return bad ? FL_NONPHYS : 0;
 }
 
@@ -739,7 +793,7 @@ int oracle_faces_1d(const OParams *P, const double *T, const double *W, const do
 int oracle_faces_2d(const OParams *P, const double *T, const double *gx, int dir,
                     const double *W, const double *Wx, const double *Wy, const double *Wxl,
                     const double *Wyl, const double *sx, const double *sy, double dt,
-                    double *out, double *sig)
+                    double *out, double *sig, int *nfall)
 {
     Ctx c;
     ctx_init(&c, P, T, gx, W, Wx, Wy, Wxl, Wyl, sx, sy, NULL);
@@ -814,7 +868,8 @@ int oracle_faces_2d(const OParams *P, const double *T, const double *gx, int dir
 
     /* faces f in [0, na] (face between cells f-1 and f), rows b in [0, nb) */
     size_t nf = (size_t)na + 1;
-#pragma omp parallel for reduction(| : bad) schedule(static)
+    int nf_total = 0;
+#pragma omp parallel for reduction(| : bad) reduction(+ : nf_total) schedule(static)
     for (int b = 0; b < nb; b++) {
         int bb = b - B0;
         for (int f = 0; f <= na; f++) {
@@ -856,6 +911,12 @@ int oracle_faces_2d(const OParams *P, const double *T, const double *gx, int dir
                         S[side].D[5][v] = at * wnt / ht;
                     }
                 }
+                if (P->pt_fallback)
+                    for (int side = 0; side < 2; side++) {
+                        double avg[4];
+                        for (int v = 0; v < nv; v++) avg[v] = CV(kW, vmap[v], 0, side == 0 ? f - 1 : f, b);
+                        nf_total += point_fallback(&c, &S[side], avg);
+                    }
                 double o[5][4];
                 if (!kinetic_point(&c, &S[0], &S[1], dt, o)) bad = 1;
                 /* out index: dir 0 -> [k][v][b][f][l] with b=j, f=i-face; dir 1 -> [k][v][f][b][l] */
@@ -872,6 +933,7 @@ int oracle_faces_2d(const OParams *P, const double *T, const double *gx, int dir
     }
     free(la);
     free(fr);
+    if (nfall) *nfall = nf_total;
 #undef CV
 #undef SN
 #undef ST

@@ -21,6 +21,8 @@ FP64, FP32_BULK = 0, 1
 TAU_ZERO, TAU_HGKS, TAU_NS = 0, 1, 2
 DFF_LAG_STEP, DFF_LAG_STAGE = 0, 1
 BC_PERIODIC, BC_TRANSMISSIVE, BC_FIXED, BC_REFLECTIVE, BC_NOSLIP = 0, 1, 2, 3, 4
+BC_INFLOW, BC_INFLOW_REFLECTIVE = 5, 6
+PT_FALLBACK_OFF, PT_FALLBACK_FIRST_ORDER = 0, 1
 EINVAL, ENOMEM, ECUDA, ENONPHYS, ETIMEOUT, ENOTSUP = -1, -2, -3, -4, -5, -6
 
 EXPORTS = ("cgks_default_params", "cgks_init_mesh", "cgks_set_state", "cgks_set_state_device",
@@ -29,7 +31,7 @@ EXPORTS = ("cgks_default_params", "cgks_init_mesh", "cgks_set_state", "cgks_set_
            "cgks_destroy", "cgks_strerror", "cgks_batch_init", "cgks_batch_set_state",
            "cgks_batch_step", "cgks_batch_sync", "cgks_batch_get_state", "cgks_batch_destroy",
            "cgks_stencil_row", "cgks_profile_step", "cgks_step_1d_noalloc", "cgks_autotune",
-           "cgks_batch_autotune")
+           "cgks_batch_autotune", "cgks_set_time")
 
 
 class Params(ctypes.Structure):
@@ -37,12 +39,15 @@ class Params(ctypes.Structure):
                 ("tau_mode", ctypes.c_int), ("bc", ctypes.c_int * 4), ("gamma", ctypes.c_double),
                 ("cfl", ctypes.c_double), ("sigma_thres", ctypes.c_double), ("gamma_hi", ctypes.c_double),
                 ("gamma_lo", ctypes.c_double), ("weno_eps", ctypes.c_double), ("tau_c1", ctypes.c_double),
-                ("tau_c2", ctypes.c_double), ("mu", ctypes.c_double), ("dff_lag", ctypes.c_int)]
+                ("tau_c2", ctypes.c_double), ("mu", ctypes.c_double), ("dff_lag", ctypes.c_int),
+                ("pt_fallback", ctypes.c_int), ("bc_state", ctypes.c_double * 32),
+                ("bc_split", ctypes.c_double * 8)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("steps", ctypes.c_longlong), ("min_rho", ctypes.c_double),
-                ("min_p", ctypes.c_double), ("mass", ctypes.c_double * 4), ("branch", ctypes.c_longlong * 4)]
+                ("min_p", ctypes.c_double), ("mass", ctypes.c_double * 4), ("branch", ctypes.c_longlong * 4),
+                ("fallbacks", ctypes.c_longlong)]
 
 
 class CgksError(RuntimeError):
@@ -71,6 +76,7 @@ def lib():
         L.cgks_set_ghost.argtypes = [vp, vp]
         L.cgks_compute_dt.argtypes = [vp, dp]
         L.cgks_step.argtypes = [vp, ctypes.c_double]
+        L.cgks_set_time.argtypes = [vp, ctypes.c_double]
         L.cgks_advance.argtypes = [vp, ip, ctypes.c_double]
         L.cgks_sync.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_longlong)]
         L.cgks_get_state.argtypes = [vp] + [vp] * 7
@@ -132,7 +138,12 @@ def make_params(dim, order, precision=FP64, tau_mode=TAU_ZERO, bc=(BC_PERIODIC,)
     for k in range(4):
         p.bc[k] = bc[k]
     for k, v in kw.items():
-        setattr(p, k, v)
+        if k in ("bc_state", "bc_split"):
+            # [4][2][4] inflow states and [4][2] split points, flattened in C order
+            v = np.asarray(v, dtype=np.float64).ravel().tolist()
+            getattr(p, k)[:] = v
+        else:
+            setattr(p, k, v)
     return p
 
 
@@ -250,7 +261,11 @@ class Solver:
         s = Stats()
         _check(lib().cgks_get_stats(self.h, ctypes.byref(s)), "cgks_get_stats")
         return dict(t=s.t, min_rho=s.min_rho, min_p=s.min_p, mass=list(s.mass)[: self.nv],
-                    branch=dict(zip(("ao", "r5", "r7", "r9"), list(s.branch))))
+                    branch=dict(zip(("ao", "r5", "r7", "r9"), list(s.branch))), fallbacks=s.fallbacks)
+
+    def set_time(self, t):
+        """Set the simulated time t^n of the next step (restarts, inflow split points)."""
+        _check(lib().cgks_set_time(self.h, float(t)), "cgks_set_time")
 
     def autotune(self):
         """Pick each stage kernel's block size by timing it on the current state."""

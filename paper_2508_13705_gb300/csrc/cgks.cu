@@ -62,7 +62,7 @@ int load_tables()
     return CGKS_OK;
 }
 
-Kfns pick_kfns(int dim, int order, int prec, int tau_mode, const int bc[4])
+Kfns pick_kfns(int dim, int order, int prec, int tau_mode, const int bc[4], int pt_fallback)
 {
     int M = (order - 1) / 2;
     Kfns k;
@@ -72,6 +72,9 @@ Kfns pick_kfns(int dim, int order, int prec, int tau_mode, const int bc[4])
     // the flux instances of the mesh's collision-time mode
     if (tau_mode == CGKS_TAU_HGKS || tau_mode == CGKS_TAU_NS)
         for (int c = 0; c < 2; ++c) { k.flux1v[c] = k.flux1h[c]; k.flux2v[c] = k.flux2h[c]; }
+    // the point fallback has one instance (tau > 0, uncapped)
+    if (pt_fallback == CGKS_PT_FALLBACK_FIRST_ORDER)
+        for (int c = 0; c < 2; ++c) { k.flux1v[c] = k.flux1p; k.flux2v[c] = k.flux2p; }
     k.flux1 = k.flux1v[0];
     k.flux2 = k.flux2v[0];
     // stencil kernels with the wall ghost rules only where a side is a wall
@@ -212,10 +215,24 @@ int validate(const cgks_params* p)
     if (!(p->gamma > 1.0) || !(p->cfl > 0.0) || !(p->sigma_thres > 0.0)) return CGKS_EINVAL;
     if (!(p->gamma_hi > 0.0 && p->gamma_hi < 1.0) || !(p->gamma_lo > 0.0 && p->gamma_lo < 1.0)) return CGKS_EINVAL;
     if (!(p->weno_eps > 0.0)) return CGKS_EINVAL;
+    if (p->pt_fallback != CGKS_PT_FALLBACK_OFF && p->pt_fallback != CGKS_PT_FALLBACK_FIRST_ORDER) return CGKS_EINVAL;
     for (int s = 0; s < 4; ++s) {
-        if (p->bc[s] < 0 || p->bc[s] > CGKS_BC_NOSLIP) return CGKS_EINVAL;
+        if (p->bc[s] < 0 || p->bc[s] > CGKS_BC_INFLOW_REFLECTIVE) return CGKS_EINVAL;
         if (p->bc[s] == CGKS_BC_FIXED && (p->dim == 2 || s >= 2)) return CGKS_EINVAL;
+        if (p->bc[s] == CGKS_BC_INFLOW || p->bc[s] == CGKS_BC_INFLOW_REFLECTIVE) {
+            if (p->dim != 2) return CGKS_EINVAL;
+            if (!std::isfinite(p->bc_split[s][0]) || !std::isfinite(p->bc_split[s][1])) return CGKS_EINVAL;
+            for (int h = 0; h < 2; ++h) {
+                const double* q = p->bc_state[s][h];
+                double rho = q[0];
+                if (!(rho > 0.0) || !std::isfinite(rho)) return CGKS_EINVAL;
+                double pr = (p->gamma - 1.0) * (q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]) / rho);
+                if (!(pr > 0.0) || !std::isfinite(pr)) return CGKS_EINVAL;
+            }
+        }
     }
+    // the fallback is compiled into the collision-time (tau > 0) flux only
+    if (p->pt_fallback && p->tau_mode == CGKS_TAU_ZERO) return CGKS_ENOTSUP;
     return CGKS_OK;
 }
 
@@ -289,7 +306,7 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return CGKS_ECUDA; }
         b->own_stream = true;
     }
-    b->k = pick_kfns(p->dim, p->order, p->precision, p->tau_mode, p->bc);
+    b->k = pick_kfns(p->dim, p->order, p->precision, p->tau_mode, p->bc, p->pt_fallback);
     std::vector<Layout> L(n);
     size_t total = 0;
     std::vector<size_t> base(n);
@@ -311,6 +328,11 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         for (int s = 0; s < 4; ++s) g.bc[s] = p->bc[s];
         g.tau_mode = p->tau_mode;
         g.dff_lag = p->dff_lag;
+        g.pf = p->pt_fallback;
+        g.x0 = ext[4 * k];
+        g.y0 = p->dim == 2 ? ext[4 * k + 2] : 0.0;
+        std::memcpy(g.bcs, p->bc_state, sizeof(g.bcs));
+        std::memcpy(g.bcx, p->bc_split, sizeof(g.bcx));
         g.dx = (ext[4 * k + 1] - ext[4 * k]) / nx[k];
         g.dy = p->dim == 2 ? (ext[4 * k + 3] - ext[4 * k + 2]) / ny[k] : 1.0;
         g.gamma = p->gamma; g.K = K; g.thr = p->sigma_thres; g.ghi = p->gamma_hi; g.glo = p->gamma_lo;
@@ -349,6 +371,8 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         g.branch = (unsigned long long*)(sc + 40);
         g.dtf = (float*)(sc + 72);
         g.ghost = (const double*)(sc + 80);  // 36 doubles of fixed ghost cells (1-D)
+        g.tn = (double*)(sc + 368);
+        g.nfall = (unsigned long long*)(sc + 376);
     }
     // prefix arrays
     b->off.assign((size_t)W_COUNT * (n + 1), 0);
@@ -433,6 +457,8 @@ int set_state_impl(cgks_batch* b, int k, const double* W, const double* Wx, cons
     }
     CK(cudaMemsetAsync(g.status, 0, 4, s));
     CK(cudaMemsetAsync(g.t, 0, 8, s));
+    CK(cudaMemsetAsync(g.tn, 0, 8, s));
+    CK(cudaMemsetAsync(g.nfall, 0, 8, s));
     long long mx = LLONG_MAX;
     CK(cudaMemcpyAsync(g.bad, &mx, 8, cudaMemcpyHostToDevice, s));
     if (sx) {
@@ -524,8 +550,13 @@ int autotune(cgks_batch* b, int* out)
     const int kinds[5] = {W_LINES, W_NORMAL, W_FLUX, W_FLUX, W_CELLS};
     const int stages[5] = {1, 1, 0, 0, 0};
     const bool has_stage[5] = {true, true, false, false, false};
-    std::vector<double> t_saved(b->n);
-    for (int k = 0; k < b->n; ++k) CK(cudaMemcpy(&t_saved[k], b->host[k].t, 8, cudaMemcpyDeviceToHost));
+    std::vector<double> t_saved(b->n), tn_saved(b->n);
+    std::vector<unsigned long long> nf_saved(b->n);
+    for (int k = 0; k < b->n; ++k) {
+        CK(cudaMemcpy(&t_saved[k], b->host[k].t, 8, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&tn_saved[k], b->host[k].tn, 8, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&nf_saved[k], b->host[k].nfall, 8, cudaMemcpyDeviceToHost));
+    }
     // a CFL time step so that every kernel sees the data of a real step
     int r = launch(b, (const void*)b->k.cfl, W_CELLS, 6, 0, false);
     if (r) return r;
@@ -547,6 +578,7 @@ int autotune(cgks_batch* b, int* out)
         const void* var[2] = {fns[qq], nullptr};
         if (q == 2) { var[0] = (const void*)b->k.flux1v[0]; var[1] = (const void*)b->k.flux1v[1]; }
         if (q == 3) { var[0] = (const void*)b->k.flux2v[0]; var[1] = (const void*)b->k.flux2v[1]; }
+        if (var[1] == var[0]) var[1] = nullptr;
         int best_t = b->threads[q], best_g = b->grid[q];
         const void* best_f = fns[qq];
         float best = 1e30f;
@@ -583,14 +615,18 @@ int autotune(cgks_batch* b, int* out)
     b->grid[5] = grid_for(b, (const void*)b->k.upd2, b->threads[5]);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    for (int k = 0; k < b->n; ++k) CK(cudaMemcpy(b->host[k].t, &t_saved[k], 8, cudaMemcpyHostToDevice));
+    for (int k = 0; k < b->n; ++k) {
+        CK(cudaMemcpy(b->host[k].t, &t_saved[k], 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b->host[k].tn, &tn_saved[k], 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b->host[k].nfall, &nf_saved[k], 8, cudaMemcpyHostToDevice));
+    }
     for (int g = 0; g < 2; ++g)
         if (b->gexec[g]) { cudaGraphExecDestroy(b->gexec[g]); b->gexec[g] = nullptr; }
     if (out) {
         for (int q = 0; q < 6; ++q) out[q] = b->threads[q];
         // register-capped flux variants are reported as a negative block size
-        if ((const void*)b->k.flux1 == (const void*)b->k.flux1v[1]) out[2] = -out[2];
-        if ((const void*)b->k.flux2 == (const void*)b->k.flux2v[1]) out[3] = -out[3];
+        if (b->k.flux1v[1] != b->k.flux1v[0] && b->k.flux1 == b->k.flux1v[1]) out[2] = -out[2];
+        if (b->k.flux2v[1] != b->k.flux2v[0] && b->k.flux2 == b->k.flux2v[1]) out[3] = -out[3];
     }
     return CGKS_OK;
 }
@@ -674,6 +710,15 @@ int cgks_set_ghost(cgks_solver* s, const double* ghost)
 {
     if (!s || !ghost || s->b->dim != 1) return CGKS_EINVAL;
     CK(cudaMemcpy((void*)s->b->host[0].ghost, ghost, 36 * sizeof(double), cudaMemcpyHostToDevice));
+    return CGKS_OK;
+}
+
+int cgks_set_time(cgks_solver* s, double t)
+{
+    if (!s || !std::isfinite(t)) return CGKS_EINVAL;
+    cgks_batch* b = s->b;
+    CK(cudaMemcpyAsync(b->host[0].t, &t, 8, cudaMemcpyHostToDevice, b->stream));
+    CK(cudaMemcpyAsync(b->host[0].tn, &t, 8, cudaMemcpyHostToDevice, b->stream));
     return CGKS_OK;
 }
 
@@ -777,6 +822,9 @@ int cgks_get_stats(cgks_solver* s, cgks_stats* st)
     unsigned long long br[4];
     CK(cudaMemcpy(br, g.branch, sizeof(br), cudaMemcpyDeviceToHost));
     for (int q = 0; q < 4; ++q) st->branch[q] = (long long)br[q];
+    unsigned long long nf = 0;
+    CK(cudaMemcpy(&nf, g.nfall, 8, cudaMemcpyDeviceToHost));
+    st->fallbacks = (long long)nf;
     st->min_rho = 1e300;
     st->min_p = 1e300;
     for (size_t c = 0; c < P; ++c) {
@@ -995,6 +1043,8 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     for (int q = 0; q < 4; ++q) g.bc[q] = p->bc[q];
     g.tau_mode = p->tau_mode;
     g.dff_lag = p->dff_lag;
+    g.pf = p->pt_fallback;
+    g.x0 = x0;
     g.dx = (x1 - x0) / nx; g.dy = 1.0;
     g.gamma = p->gamma; g.K = (3.0 - p->gamma) / (p->gamma - 1.0); g.thr = p->sigma_thres;
     g.ghi = p->gamma_hi; g.glo = p->gamma_lo; g.eps = p->weno_eps; g.c1 = p->tau_c1; g.c2 = p->tau_c2;
@@ -1017,6 +1067,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     g.dt = (double*)sc; g.t = (double*)(sc + 8); g.status = (unsigned*)(sc + 16);
     g.bad = (long long*)(sc + 24); g.smax = (unsigned long long*)(sc + 32);
     g.branch = (unsigned long long*)(sc + 40); g.dtf = (float*)(sc + 72); g.ghost = (const double*)(sc + 80);
+    g.tn = (double*)(sc + 368); g.nfall = (unsigned long long*)(sc + 376);
     long long off[W_COUNT * 2];
     for (int kind = 0; kind < W_COUNT; ++kind) { off[2 * kind] = 0; off[2 * kind + 1] = items(kind, 1, 1, nx, 1); }
     Mesh* dmesh = (Mesh*)(base + oM);
@@ -1031,7 +1082,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     if (sigma_in && sigma_in != sigma_out)
         CK(cudaMemcpyAsync(sigma_out, sigma_in, (size_t)(nx + 1) * 8, cudaMemcpyDeviceToDevice, st));
     if (dt > 0.0) CK(cudaMemcpyAsync(g.dt + 0, &dt, 8, cudaMemcpyHostToDevice, st));
-    Kfns k = pick_kfns(1, p->order, p->precision, p->tau_mode, p->bc);
+    Kfns k = pick_kfns(1, p->order, p->precision, p->tau_mode, p->bc, p->pt_fallback);
     int nsm = 1;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     auto go = [&](const void* fn, int kind, int stage, bool has_stage, int threads) -> int {

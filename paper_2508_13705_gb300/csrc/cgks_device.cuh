@@ -33,7 +33,8 @@
 
 namespace cgks {
 
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_FIXED = 2, BC_REFLECTIVE = 3, BC_NOSLIP = 4 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_FIXED = 2, BC_REFLECTIVE = 3, BC_NOSLIP = 4,
+       BC_INFLOW = 5, BC_INFLOW_REFLECTIVE = 6 };
 enum { ST_S0 = 0, ST_S1 = 1, ST_S2 = 2, ST_R5 = 3, ST_R7 = 4, ST_R9 = 5 };
 enum { STATUS_NONPHYS = 1u };
 
@@ -63,9 +64,13 @@ struct Mesh {
     int bc[4];
     int tau_mode;
     int dff_lag;                    // 0: sigma of step n-1; 1: stage 2 uses stage 1's
+    int pf;                         // first-order fallback at non-physical face points
     double dx, dy, gamma, K, thr, ghi, glo, eps, c1, c2, cfl;
     double idx, idy;                // 1 / dx, 1 / dy
     double mu;                      // dynamic viscosity (tau_mode 2)
+    double x0, y0;                  // lower-left corner
+    double bcs[4][2][4];            // inflow ghost states per side: [0] below the split, [1] beyond
+    double bcx[4][2];               // split point along the side: bcx[0] + bcx[1] t
     float muf;
     float gf, Kf, c1f, c2f, idxf, idyf;  // FP32-bulk copies (no per-point conversions)
     long long plane;                // nx * ny
@@ -86,6 +91,8 @@ struct Mesh {
     double* dt;                     // device scalar (this mesh's step)
     float* dtf;                     // the same in FP32
     double* t;                      // device scalar (simulated time)
+    double* tn;                     // device scalar: t^n of the step in flight
+    unsigned long long* nfall;      // face-point sides that took the fallback
     unsigned* status;
     long long* bad;
     unsigned long long* smax;       // CFL reduction (bits of a positive double)
@@ -148,6 +155,23 @@ template <> __device__ __forceinline__ const float* state_planes<float>(const Me
 }
 
 __device__ __forceinline__ bool is_wall(int bc) { return bc == BC_REFLECTIVE || bc == BC_NOSLIP; }
+// sides whose ghost faces mirror sigma (a wall along all or part of the side)
+__device__ __forceinline__ bool is_mirror(int bc) { return is_wall(bc) || bc == BC_INFLOW_REFLECTIVE; }
+
+// Time at which a stage takes prescribed ghost states: t^n in stage 1, the
+// stage-2 state lives at t^n + dt/2.
+__device__ __forceinline__ double stage_time(const Mesh& g, int stage)
+{
+    return stage == 1 ? *g.tn : *g.tn + 0.5 * *g.dt;
+}
+
+// Inflow sides: is the centre of ghost row / column k, along side `side`
+// (y on the x-sides, x on the y-sides), below the split point at time tb?
+__device__ __forceinline__ bool below_split(const Mesh& g, int side, int k, double tb)
+{
+    double s = side < 2 ? g.y0 + (k + 0.5) * g.dy : g.x0 + (k + 0.5) * g.dx;
+    return s < g.bcx[side][0] + g.bcx[side][1] * tb;
+}
 
 // Sign of a ghost value mirrored across a wall with normal x (normal = 0) or
 // y (normal = 1): reflection maps q to S q(-x), S reversing the normal
@@ -161,12 +185,13 @@ __device__ __forceinline__ bool wall_flip(int kind, int v, int normal, int bc)
     return rev != dnormal;
 }
 
-// kind: 0 W, 1 Wx, 2 Wy, 3 Wx_line, 4 Wy_line (global orientation).
-// WALLS = false compiles the wall branches out: the stencil kernels have a
-// wall-free instance for meshes without walls, whose hot loops the (never
-// taken) wall code would otherwise slow down.
+// kind: 0 W, 1 Wx, 2 Wy, 3 Wx_line, 4 Wy_line (global orientation); tb: the
+// stage's time, read by inflow sides only.  Ghost rules apply x first, then y.
+// WALLS = false compiles the wall and inflow branches out: the stencil kernels
+// have an instance for meshes without them, whose hot loops the (never
+// taken) code would otherwise slow down.
 template <int D, int M, typename T, bool WALLS = true>
-__device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, int l, int i, int j)
+__device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, int l, int i, int j, double tb)
 {
     bool zero = false, neg = false;
     if (i < 0 || i >= g.nx) {
@@ -177,7 +202,10 @@ __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, in
         } else if (bc == BC_FIXED) {
             int layer = side == 0 ? (-1 - i) : (i - g.nx);
             return (T)g.ghost[((side * 3 + layer) * 2 + (kind == 0 ? 0 : 1)) * 3 + v];
-        } else if (WALLS && is_wall(bc)) {
+        } else if (WALLS && (bc == BC_INFLOW || (bc == BC_INFLOW_REFLECTIVE && below_split(g, side, j, tb)))) {
+            // prescribed state by the row's centre, zero slopes
+            return kind == 0 ? (T)g.bcs[side][below_split(g, side, j, tb) ? 0 : 1][v] : (T)0;
+        } else if (WALLS && is_mirror(bc)) {
             // ghost cell -1-k mirrors cell k; lines across x (Wy_line) swap ends
             i = i < 0 ? -1 - i : 2 * g.nx - 1 - i;
             neg = wall_flip<D>(kind, v, 0, bc);
@@ -188,10 +216,16 @@ __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, in
         }
     }
     if (D == 2 && (j < 0 || j >= g.ny)) {
-        int bc = g.bc[j < 0 ? 2 : 3];
+        int side = j < 0 ? 2 : 3;
+        int bc = g.bc[side];
+        if (WALLS && (bc == BC_INFLOW || (bc == BC_INFLOW_REFLECTIVE && below_split(g, side, i, tb)))) {
+            // prescribed state by the column's centre (after the x rule), zero slopes
+            T val = kind == 0 ? (T)g.bcs[side][below_split(g, side, i, tb) ? 0 : 1][v] : (T)0;
+            return neg ? -val : val;
+        }
         if (bc == BC_PERIODIC) {
             j = imod(j, g.ny);
-        } else if (WALLS && is_wall(bc)) {
+        } else if (WALLS && is_mirror(bc)) {
             j = j < 0 ? -1 - j : 2 * g.ny - 1 - j;
             neg = neg != wall_flip<D>(kind, v, 1, bc);
             if (kind == 3) l = M - 1 - l;
@@ -226,13 +260,13 @@ __device__ __forceinline__ double sigx(const Mesh& g, const double* sx, int f, i
     if (f < 0 || f > g.nx) {
         int bc = g.bc[f < 0 ? 0 : 1];
         if (bc == BC_PERIODIC) f = imod(f, g.nx);
-        else if (WALLS && is_wall(bc)) f = f < 0 ? -f : 2 * g.nx - f;  // beyond a wall: the mirrored face
+        else if (WALLS && is_mirror(bc)) f = f < 0 ? -f : 2 * g.nx - f;  // beyond a wall: the mirrored face
         else return 0.0;
     }
     if (D == 2 && (j < 0 || j >= g.ny)) {
         int bc = g.bc[j < 0 ? 2 : 3];
         if (bc == BC_PERIODIC) j = imod(j, g.ny);
-        else if (WALLS && is_wall(bc)) j = j < 0 ? -1 - j : 2 * g.ny - 1 - j;
+        else if (WALLS && is_mirror(bc)) j = j < 0 ? -1 - j : 2 * g.ny - 1 - j;
         else j = j < 0 ? 0 : g.ny - 1;
     }
     return sx[(long long)j * (g.nx + 1) + f];
@@ -244,13 +278,13 @@ __device__ __forceinline__ double sigy(const Mesh& g, const double* sy, int i, i
     if (f < 0 || f > g.ny) {
         int bc = g.bc[f < 0 ? 2 : 3];
         if (bc == BC_PERIODIC) f = imod(f, g.ny);
-        else if (WALLS && is_wall(bc)) f = f < 0 ? -f : 2 * g.ny - f;
+        else if (WALLS && is_mirror(bc)) f = f < 0 ? -f : 2 * g.ny - f;
         else return 0.0;
     }
     if (i < 0 || i >= g.nx) {
         int bc = g.bc[i < 0 ? 0 : 1];
         if (bc == BC_PERIODIC) i = imod(i, g.nx);
-        else if (WALLS && is_wall(bc)) i = i < 0 ? -1 - i : 2 * g.nx - 1 - i;
+        else if (WALLS && is_mirror(bc)) i = i < 0 ? -1 - i : 2 * g.nx - 1 - i;
         else i = i < 0 ? 0 : g.nx - 1;
     }
     return sy[(long long)f * g.nx + i];

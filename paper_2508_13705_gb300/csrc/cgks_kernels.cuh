@@ -36,7 +36,8 @@ __device__ __forceinline__ void local_dims(const Mesh& g, int dir, int& na, int&
 
 // cell value in local coordinates; lkind: 0 W, 1 W_n (cell), 2 W_t (cell), 3 W_n line
 template <int D, int M, typename T, bool WALLS = true>
-__device__ __forceinline__ T lcell(const Mesh& g, const T* S, int dir, int lkind, int v, int l, int a, int b)
+__device__ __forceinline__ T lcell(const Mesh& g, const T* S, int dir, int lkind, int v, int l, int a, int b,
+                                   double tb)
 {
     int kind;
     if (lkind == 0) kind = 0;
@@ -44,7 +45,7 @@ __device__ __forceinline__ T lcell(const Mesh& g, const T* S, int dir, int lkind
     else if (lkind == 2) kind = dir == 0 ? 2 : 1;
     else kind = dir == 0 ? 3 : 4;
     int i = dir == 0 ? a : b, j = dir == 0 ? b : a;
-    return cell<D, M, T, WALLS>(g, S, kind, vglob(dir, v), l, i, j);
+    return cell<D, M, T, WALLS>(g, S, kind, vglob(dir, v), l, i, j, tb);
 }
 
 // sigma of normal faces (f, b) and of tangential faces of column a (a, f)
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         if (dir == 0) { unsigned d = na + 6, q = li / d; a = (int)(li - q * d) - 3; b = (int)q - 1; }
         else { unsigned d = nb + 2, q = li / d; b = (int)(li - q * d) - 1; a = (int)q - 3; }
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
+        const double tb = WALLS ? stage_time(g, stage) : 0.0;  // inflow ghost states
         // sigma of the DFF (Sec. 3.1): of step n-1 in both stages, or, in stage 2
         // of the stage-lag reading, the face means of stage 1 of this step
         const bool lag_stage = stage == 2 && g.dff_lag;
@@ -145,8 +147,8 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
             for (int v = 0; v < 4; ++v)
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
-                    sw[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 0, v, 0, a, b + q - 2);
-                    swt[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 2, v, 0, a, b + q - 2);
+                    sw[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 0, v, 0, a, b + q - 2, tb);
+                    swt[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 2, v, 0, a, b + q - 2, tb);
                 }
         }
         // face sigma of the tangential stencil: a direct walk for interior cells
@@ -236,6 +238,7 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         else if (dir == 0) { unsigned d = na + 2, q = r / d; a = (int)(r - q * d) - 1; b = (int)q - 1; }
         else { unsigned d = nb + 2, q = r / d; b = (int)(r - q * d) - 1; a = (int)q - 1; }
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
+        const double tb = WALLS ? stage_time(g, stage) : 0.0;  // inflow ghost states
         long long cidx = cell_idx(dir, na, nb, a, b);
         long long lstr = dir == 0 ? 1 : (nb + 2);  // LA stride between normal neighbours
         DffR<R> dff;
@@ -290,7 +293,7 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) sl[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 3, v, l, a + q - 2, b);
+                    for (int q = 0; q < 5; ++q) sl[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 3, v, l, a + q - 2, b, tb);
             }
         }
         const R ghi = (R)g.ghi, glo = (R)g.glo, eps = (R)g.eps;
@@ -315,12 +318,12 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         } else {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                R qi = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a, 0);
+                R qi = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a, 0, tb);
                 R dp[10];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
-                    dp[q] = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a + q - 2, 0) - qi;
-                    dp[5 + q] = hn * cell<1, 1, R, WALLS>(g, S, 1, v, 0, a + q - 2, 0);
+                    dp[q] = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a + q - 2, 0, tb) - qi;
+                    dp[5 + q] = hn * cell<1, 1, R, WALLS>(g, S, 1, v, 0, a + q - 2, 0, tb);
                 }
                 R out[6];
                 recon<R, 6>(dff, g.oi, 0, dp, out, ghi, glo, eps);
@@ -360,8 +363,9 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
 // spilling the rest); CAP = 0 for 3 in FP32 (<= 170 registers, no spills) and
 // 1 in FP64.  The autotuner times both variants.  HG = 1 compiles the
 // collision-time terms (tau > 0); the tau = 0 instance leaves them out and
-// carries fewer live values.
-template <int D, int M, typename R, int STAGE, int CAP, int HG>
+// carries fewer live values.  PF = true compiles the first-order fallback at
+// face points whose reconstructed state is not physical (a flagged option).
+template <int D, int M, typename R, int STAGE, int CAP, int HG, bool PF = false>
 __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flux(Work w)
 {
     constexpr int NV = D + 2;
@@ -451,6 +455,25 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
                     d[3][v] = c1 * wt[v];
                     d[4][v] = c2 * wtt[v];
                     d[5][v] = c1 * wnt[v];
+                }
+            }
+            if (PF) {
+                // fallback: a side whose point state has rho <= 0 or p <= 0 takes
+                // the average of the cell it was reconstructed from, first order
+                R rho = d[0][0];
+                R m2 = d[0][1] * d[0][1] + (D == 2 ? d[0][2] * d[0][2] : (R)0);
+                R p = (gm - (R)1) * (d[0][NV - 1] - (R)0.5 * m2 / rho);
+                if (!(rho > (R)0) || !(p > (R)0)) {
+                    const R* S = state_planes<R>(g, STAGE == 1 ? 0 : 1);
+                    const double tb = stage_time(g, STAGE);
+                    int a = side == 0 ? f - 1 : f;
+#pragma unroll
+                    for (int v = 0; v < NV; ++v) {
+                        d[0][v] = lcell<D, M, R, true>(g, S, dir, 0, v, 0, a, b, tb);
+#pragma unroll
+                        for (int q = 1; q < 6; ++q) d[q][v] = (R)0;
+                    }
+                    atomicAdd(g.nfall, 1ull);
                 }
             }
             // Eq. 3.2 ingredients and the positivity test, in the precision the
@@ -918,7 +941,7 @@ __global__ void __launch_bounds__(256) k_cfl(Work w)
     }
 }
 
-// dt = cfl / smax per mesh (or the fixed value); t += dt; reset the reduction
+// dt = cfl / smax per mesh (or the fixed value); t^n = t, t += dt; reset the reduction
 template <int Unused = 0>
 __global__ void k_dt(Mesh* meshes, int n, int use_cfl, const double* fixed)
 {
@@ -934,6 +957,7 @@ __global__ void k_dt(Mesh* meshes, int n, int use_cfl, const double* fixed)
         }
         *g.dt = dt;
         *g.dtf = (float)dt;
+        *g.tn = *g.t;
         *g.t += dt;
         for (int q = 0; q < 4; ++q) g.branch[q] = 0ull;  // counts cover the latest step
     }
@@ -955,10 +979,12 @@ __global__ void k_sigma_init(Work w)
         if (dir == 0) { f = (int)(li % (g.nx + 1)); b = (int)(li / (g.nx + 1)); }
         else { b = (int)(li % g.nx); f = (int)(li / g.nx); }
         double Ws[2][4];
+        const double tb = *g.t;  // inflow ghost states at the current time
         for (int s = 0; s < 2; ++s)
             for (int v = 0; v < D + 2; ++v) {
                 int a = f - 1 + s;
-                Ws[s][v] = dir == 0 ? cell<D, 4, double>(g, g.S0, 0, v, 0, a, b) : cell<D, 4, double>(g, g.S0, 0, v, 0, b, a);
+                Ws[s][v] = dir == 0 ? cell<D, 4, double>(g, g.S0, 0, v, 0, a, b, tb)
+                                    : cell<D, 4, double>(g, g.S0, 0, v, 0, b, a, tb);
             }
         double pz[2], mn[2], mt[2];
         for (int s = 0; s < 2; ++s) {

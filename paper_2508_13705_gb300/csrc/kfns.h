@@ -13,6 +13,7 @@ struct Kfns {
     KStage convert;  // FP32-bulk state copies (to_float = 1: FP64 -> float planes)
     KOne flux1v[2], flux2v[2];  // flux variants: [0] uncapped, [1] register-capped (tau = 0)
     KOne flux1h[2], flux2h[2];  // the same with the collision-time terms (tau > 0)
+    KOne flux1p, flux2p;        // tau > 0 with the first-order fallback at face points
     int (*upload)(const CgksTables* t3, const TabF* f3);  // constant tables of this unit
 };
 Kfns kfns_1_1_d();

@@ -29,6 +29,8 @@ Kfns make_kfns()
     k.flux2h[0] = k_flux<D, M, R, 2, 0, 1>;
     k.flux1h[1] = k_flux<D, M, R, 1, 1, 1>;
     k.flux2h[1] = k_flux<D, M, R, 2, 1, 1>;
+    k.flux1p = k_flux<D, M, R, 1, 0, 1, true>;
+    k.flux2p = k_flux<D, M, R, 2, 0, 1, true>;
     k.flux1 = k.flux1v[0];
     k.flux2 = k.flux2v[0];
     if (D == 2) { k.upd1 = (KOne)k_update2<M, R, 1>; k.upd2 = (KOne)k_update2<M, R, 2>; }

@@ -20,6 +20,8 @@ Workloads (shapes follow the paper's test problems):
 * ``vortex_2d``         isentropic vortex (strength 5) on periodic [0, 10]^2
 * ``quadrants_2d``      four-quadrant Riemann problem, seeded random states
 * ``batch_2d``          seeded uneven meshes: Fourier modes + planar shock
+* ``double_mach``       Sec. 4.8 double Mach reflection, with its boundary sides
+* ``oblique_shock``     its Mach 10 shock alone, translating between inflow sides
 """
 import numpy as np
 
@@ -306,3 +308,69 @@ def batch_instance(spec, order, gamma=1.4, nq=4):
         Wxl[:, :, post, :] = 0.0
         Wyl[:, :, post, :] = 0.0
     return W, Wx, Wy, Wxl, Wyl
+
+
+# Boundary codes of the C ABI (the oracle uses the same numbers)
+_BC_TRANSMISSIVE, _BC_INFLOW, _BC_INFLOW_REFLECTIVE = 1, 5, 6
+# Mach 10 shock of Sec. 4.8: speed 10 into gas at rest (sound speed 1), its
+# front at 60 degrees to the x axis, so it crosses every horizontal line at
+# 10 / sin 60 = 20 / sqrt 3
+SHOCK_SPEED_X = 20.0 / np.sqrt(3.0)
+
+
+def _mach10_states(gamma):
+    s3 = np.sqrt(3.0)
+    pre = np.asarray(_cons(1.4, 0.0, 0.0, 1.0, gamma, 2), dtype=np.float64)
+    post = np.asarray(_cons(8.0, 4.125 * s3, -4.125, 116.5, gamma, 2), dtype=np.float64)
+    return pre, post
+
+
+def _oblique_shock(nx, ny, extent, xa, order, gamma):
+    """Cell states (by the cell centre, zero slopes) of the Mach 10 shock whose
+    front passes through (xa, 0) at 60 degrees: post-shock gas left of it."""
+    pre, post = _mach10_states(gamma)
+    x0, x1, y0, y1 = extent
+    hx, hy = (x1 - x0) / nx, (y1 - y0) / ny
+    xc = x0 + (np.arange(nx) + 0.5) * hx
+    yc = y0 + (np.arange(ny) + 0.5) * hy
+    ahead = yc[:, None] < np.sqrt(3.0) * (xc[None, :] - xa)
+    W = np.where(ahead[None], pre.reshape(4, 1, 1), post.reshape(4, 1, 1))
+    m = len(line_nodes(order))
+    z = np.zeros((4, ny, nx))
+    return (np.ascontiguousarray(W), z.copy(), z.copy(), np.zeros((m, 4, ny, nx)), np.zeros((m, 4, ny, nx)))
+
+
+def double_mach(nx, ny, order, gamma=1.4):
+    """Double Mach reflection (Sec. 4.8) on [0,4] x [0,1]: a Mach 10 shock
+    through (1/6, 0) at 60 degrees to the x axis, gas at rest (1.4, 0, 0, 1)
+    ahead of it and (8, 4.125 sqrt 3, -4.125, 116.5) behind; cell states by the
+    cell centre, zero slopes.  Returns the state tuple and the boundary
+    keywords: inflow of the post-shock state on the left, transmissive right,
+    post-shock state below x = 1/6 and a slip wall beyond it at the bottom,
+    and at the top the exact shock position 1/6 + (1 + 20 t) / sqrt 3 splitting
+    post-shock from pre-shock ghost cells."""
+    extent = (0.0, 4.0, 0.0, 1.0)
+    state = _oblique_shock(nx, ny, extent, 1.0 / 6.0, order, gamma)
+    pre, post = _mach10_states(gamma)
+    bc_state = [[post, post], [post, post], [post, post], [post, pre]]
+    bc_split = [[0.0, 0.0], [0.0, 0.0], [1.0 / 6.0, 0.0], [1.0 / 6.0 + 1.0 / np.sqrt(3.0), SHOCK_SPEED_X]]
+    kw = dict(extent=extent, bc=(_BC_INFLOW, _BC_TRANSMISSIVE, _BC_INFLOW_REFLECTIVE, _BC_INFLOW),
+              bc_state=np.asarray(bc_state, dtype=np.float64), bc_split=np.asarray(bc_split, dtype=np.float64))
+    return state, kw
+
+
+def oblique_shock(nx, ny, order, xa=0.3, height=0.5, speed=SHOCK_SPEED_X, gamma=1.4):
+    """The Mach 10 shock of Sec. 4.8 alone, translating through [0,1] x
+    [0,height] from (xa, 0): every side is an inflow side, left post-shock,
+    right pre-shock, and below and above the shock's position on that side,
+    xa + (y + 20 t) / sqrt 3, splits post- from pre-shock ghost cells (``speed``
+    replaces 20 / sqrt 3 to move the split wrongly).  The exact solution is the
+    translated shock."""
+    extent = (0.0, 1.0, 0.0, height)
+    state = _oblique_shock(nx, ny, extent, xa, order, gamma)
+    pre, post = _mach10_states(gamma)
+    bc_state = [[post, post], [pre, pre], [post, pre], [post, pre]]
+    bc_split = [[0.0, 0.0], [0.0, 0.0], [xa, speed], [xa + height / np.sqrt(3.0), speed]]
+    kw = dict(extent=extent, bc=(_BC_INFLOW,) * 4,
+              bc_state=np.asarray(bc_state, dtype=np.float64), bc_split=np.asarray(bc_split, dtype=np.float64))
+    return state, kw
