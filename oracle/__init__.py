@@ -56,6 +56,23 @@ def build(force=False):
     return _SO
 
 
+_SO_COUNT = os.path.join(_BUILD, "liboracle_count.so")
+
+
+def build_tally(force=False):
+    """Compile the operation-counting build of the same C source (flopcount.cpp)."""
+    srcs = [os.path.join(_HERE, "cgks_oracle.c"), os.path.join(_HERE, "flopcount.cpp")]
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_SO_COUNT) and all(
+            os.path.getmtime(_SO_COUNT) >= os.path.getmtime(f) for f in srcs):
+        return _SO_COUNT
+    tmp = _SO_COUNT + ".tmp%d" % os.getpid()
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared", "-w",
+                           "-o", tmp, srcs[1]], cwd=_HERE)
+    os.replace(tmp, _SO_COUNT)
+    return _SO_COUNT
+
+
 class OParams(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("order", ctypes.c_int), ("m", ctypes.c_int),
                 ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("bc", ctypes.c_int * 4),
@@ -87,6 +104,8 @@ def lib():
         _lib.oracle_moments.argtypes = [P, dp, dp, dp, dp]
         _lib.oracle_micro_slope.argtypes = [P, dp, dp, dp]
         _lib.oracle_recon.argtypes = [P, dp, dp, dp, dp]
+        _lib.oracle_smoothness.argtypes = [dp, ctypes.c_int]
+        _lib.oracle_smoothness.restype = ctypes.c_double
     return _lib
 
 
@@ -435,6 +454,12 @@ class Oracle:
         lib().oracle_micro_slope(ctypes.byref(self.P), _p(np.ascontiguousarray(W, dtype=np.float64)),
                                  _p(np.ascontiguousarray(b, dtype=np.float64)), _p(a))
         return a
+
+    def smoothness(self, poly, deg):
+        """Eq. 3.13 of a polynomial given by its 9 coefficients in xi."""
+        p = np.zeros(9)
+        p[:len(poly)] = poly
+        return lib().oracle_smoothness(_p(p), deg)
 
     def recon(self, d, sig6):
         """ASE-DFF polynomial (9 coefficients in xi) of one cell and the branch taken."""

@@ -744,7 +744,7 @@ int oracle_faces_1d(const OParams *P, const double *T, const double *W, const do
     int nx = P->nx, nv = 3, bad = 0;
     size_t nf = (size_t)nx + 1;
     /* Step 2 (the only step in 1-D): reconstruct cells -1..nx */
-    double *fl = calloc((nx + 2) * 2 * 3 * 4, sizeof(double)); /* [cell][side][deriv][v] */
+    double *fl = (double *)calloc((nx + 2) * 2 * 3 * 4, sizeof(double)); /* [cell][side][deriv][v] */
     for (int i = -1; i <= nx; i++) {
         double s4[6] = {sigx(&c, i - 2, 0), sigx(&c, i - 1, 0), sigx(&c, i, 0), sigx(&c, i + 1, 0), sigx(&c, i + 2, 0), sigx(&c, i + 3, 0)};
         for (int v = 0; v < nv; v++) {
@@ -813,7 +813,7 @@ int oracle_faces_2d(const OParams *P, const double *T, const double *gx, int dir
     /* Step 1: line averages along the normal direction at the m Gauss lines,
      * for cells a in [-3, na+2], b in [-1, nb]: tangential ASE-DFF. */
     int A0 = -3, NA = na + 6, B0 = -1, NB = nb + 2;
-    double *la = malloc((size_t)NA * NB * m * nv * sizeof(double)); /* [b][a][l][v] local v */
+    double *la = (double *)malloc((size_t)NA * NB * m * nv * sizeof(double)); /* [b][a][l][v] local v */
     int bad = 0;
 #pragma omp parallel for schedule(static)
     for (int bb = 0; bb < NB; bb++) {
@@ -834,7 +834,7 @@ int oracle_faces_2d(const OParams *P, const double *T, const double *gx, int dir
     /* Step 2: normal ASE-DFF on the line data, cells a in [-1, na], rows b in [-1, nb].
      * fr[b][a][side][l][deriv][v]: side 0 = value at the cell's +1/2 face, 1 = at its -1/2 face */
     int CA0 = -1, NCA = na + 2;
-    double *fr = malloc((size_t)NB * NCA * 2 * m * 3 * nv * sizeof(double));
+    double *fr = (double *)malloc((size_t)NB * NCA * 2 * m * 3 * nv * sizeof(double));
 #define FR(bb, ca, s, l, nd, v) fr[(((((size_t)(bb) * NCA + (ca)) * 2 + (s)) * m + (l)) * 3 + (nd)) * nv + (v)]
 #pragma omp parallel for schedule(static)
     for (int bb = 0; bb < NB; bb++) {
@@ -994,6 +994,12 @@ int oracle_micro_slope(const OParams *P, const double *W, const double *b, doubl
     int ok = maxw_from_W(&c, W, &M);
     micro_slope(&c, &M, b, a);
     return ok ? 0 : FL_NONPHYS;
+}
+
+/* Smoothness indicator of Eq. 3.13 for the pin tests (unit coordinate) */
+double oracle_smoothness(const double *p, int deg)
+{
+    return smoothness(p, deg);
 }
 
 /* ASE-DFF polynomial of one cell for the pin tests */
