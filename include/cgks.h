@@ -98,7 +98,9 @@ extern "C" {
                                    precision) takes the average of the cell it was
                                    reconstructed from, with every derivative zero; sigma
                                    then comes from the states used; counted in
-                                   cgks_stats.fallbacks */
+                                   cgks_stats.fallbacks.  Compiled into the flux of
+                                   the collision-time modes only: with CGKS_TAU_ZERO
+                                   it is rejected with CGKS_ENOTSUP */
 
 typedef struct {
     int dim;            /* 1 or 2 */
@@ -152,8 +154,8 @@ int cgks_default_params(cgks_params* p, int dim, int order);
  * split is not finite, a wall or inflow side across fewer than 3 cells,
  * pt_fallback not 0/1,
  * a mesh with 2^31 or more face Gauss points: about 16000^2 cells at order 9,
- * more than the device memory holds), CGKS_ENOMEM, CGKS_ECUDA.  On error *out
- * is NULL. */
+ * more than the device memory holds), CGKS_ENOTSUP (pt_fallback with
+ * CGKS_TAU_ZERO), CGKS_ENOMEM, CGKS_ECUDA.  On error *out is NULL. */
 int cgks_init_mesh(cgks_solver** out, const cgks_params* p, int nx, int ny,
                    double x0, double x1, double y0, double y1, void* stream);
 
@@ -174,6 +176,9 @@ int cgks_set_state_device(cgks_solver* s, const double* W, const double* Wx, con
 
 /* Set the simulated time (the t^n of the next step), e.g. to resume a run or
  * to place the split points of inflow sides; enqueued on the solver's stream.
+ * If the last set_state initialised sigma (NULL sigma arrays) and no step has
+ * run since, sigma is initialised again with the ghost states of inflow sides
+ * taken at t, as if the state had been set at time t.
  * CGKS_EINVAL for a NULL solver or a non-finite t. */
 int cgks_set_time(cgks_solver* s, double t);
 
@@ -248,6 +253,15 @@ int cgks_batch_init(cgks_batch** out, const cgks_params* p, int n, const int* nx
                     const double* ext, void* stream);
 int cgks_batch_set_state(cgks_batch* b, int k, const double* W, const double* Wx, const double* Wy,
                          const double* Wx_line, const double* Wy_line);
+/* Device-pointer variants for instance k (same layouts), enqueued on the
+ * batch's stream without waiting.  set: sigma is initialised from the cell
+ * averages and the state's positivity is checked on the device; a
+ * non-physical state is reported by cgks_batch_sync.  get: FP64 copies of the
+ * state (upcast from the float planes in the FP32-bulk form). */
+int cgks_batch_set_state_device(cgks_batch* b, int k, const double* W, const double* Wx, const double* Wy,
+                                const double* Wx_line, const double* Wy_line);
+int cgks_batch_get_state_device(cgks_batch* b, int k, double* W, double* Wx, double* Wy,
+                                double* Wx_line, double* Wy_line);
 /* one step of all instances; dt[k] > 0 fixed per instance, or NULL: each
  * instance takes its own CFL dt on the device. */
 int cgks_batch_step(cgks_batch* b, const double* dt);
@@ -276,11 +290,15 @@ void cgks_batch_destroy(cgks_batch* b);
  * dt <= 0 the CFL rule; status_out (device unsigned int, may be NULL)
  * receives the step's status word (nonzero: non-physical state met).  The
  * work is enqueued on `stream` (NULL: the legacy default stream) and the call
- * returns without waiting.
+ * returns without waiting.  It enqueues kernel launches and device-to-device
+ * copies only: the descriptor and dt travel as kernel arguments, so no host
+ * memory is read after the call returns.  With CGKS_PT_FALLBACK_FIRST_ORDER
+ * the fallback runs but its count is not reported by this entry point.
  *
  * The first call on a device does its set-up there (finds the scratch array's
  * device address, loads the reconstruction tables): make that first call
- * before any stream capture.  Every call uses the same scratch array and
+ * before any stream capture.  The set-up is guarded by a lock, so first calls
+ * from several host threads are safe.  Every call uses the same scratch array and
  * clears the parts that must start at zero; calls that overlap on the GPU
  * (different streams, or devices sharing nothing but this array's contents
  * per device) race on it and must be serialised by the caller. */

@@ -31,7 +31,8 @@ EXPORTS = ("cgks_default_params", "cgks_init_mesh", "cgks_set_state", "cgks_set_
            "cgks_destroy", "cgks_strerror", "cgks_batch_init", "cgks_batch_set_state",
            "cgks_batch_step", "cgks_batch_sync", "cgks_batch_get_state", "cgks_batch_destroy",
            "cgks_stencil_row", "cgks_profile_step", "cgks_step_1d_noalloc", "cgks_autotune",
-           "cgks_batch_autotune", "cgks_set_time")
+           "cgks_batch_autotune", "cgks_set_time", "cgks_batch_set_state_device",
+           "cgks_batch_get_state_device")
 
 
 class Params(ctypes.Structure):
@@ -92,6 +93,8 @@ def lib():
         L.cgks_batch_step.argtypes = [vp, vp]
         L.cgks_batch_sync.argtypes = [vp]
         L.cgks_batch_get_state.argtypes = [vp, ip] + [vp] * 5
+        L.cgks_batch_set_state_device.argtypes = [vp, ip] + [vp] * 5
+        L.cgks_batch_get_state_device.argtypes = [vp, ip] + [vp] * 5
         L.cgks_batch_destroy.argtypes = [vp]
         L.cgks_batch_destroy.restype = None
         L.cgks_stencil_row.argtypes = [ip, ip, ip, dp]
@@ -323,6 +326,16 @@ class Batch:
         arrs = [_host(W, c), _host(Wx, c), _host(Wy, c), _host(Wx_line, (self.m,) + c),
                 _host(Wy_line, (self.m,) + c)]
         _check(lib().cgks_batch_set_state(self.h, k, *[a[1] for a in arrs]), "cgks_batch_set_state")
+
+    def set_state_device(self, k, W, Wx, Wy, Wx_line, Wy_line):
+        """Instance k from float64 CUDA tensors, enqueued on the batch's stream."""
+        _check(lib().cgks_batch_set_state_device(self.h, k, *[_dev(t) for t in (W, Wx, Wy, Wx_line, Wy_line)]),
+               "cgks_batch_set_state_device")
+
+    def get_state_device(self, k, out):
+        """Instance k into preallocated float64 CUDA tensors (dict keyed W, Wx, Wy, Wx_line, Wy_line)."""
+        _check(lib().cgks_batch_get_state_device(self.h, k, *[_dev(out.get(n)) for n in (
+            "W", "Wx", "Wy", "Wx_line", "Wy_line")]), "cgks_batch_get_state_device")
 
     def step(self, dt=None):
         if dt is None:

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -28,9 +29,11 @@ using namespace cgks;
 namespace {
 
 int g_tables_device = -1;  // device whose constant tables are loaded
+std::mutex g_tables_mu;     // first uses from several host threads load the tables once
 
 int load_tables()
 {
+    std::lock_guard<std::mutex> lock(g_tables_mu);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return CGKS_ECUDA;
     if (g_tables_device == dev) return CGKS_OK;
@@ -108,6 +111,7 @@ struct cgks_batch {
     int kernels_per_step = 0;
     bool state_set = false;
     bool own_stream = false;
+    bool sigma_pending = false;  // sigma was initialised by set_state and no step has run since
 };
 
 struct cgks_solver {
@@ -690,6 +694,7 @@ int cgks_set_state(cgks_solver* s, const double* W, const double* Wx, const doub
     int r = set_state_impl(s->b, 0, W, Wx, Wy, Wx_line, Wy_line, sigma_x, sigma_y, cudaMemcpyHostToDevice, true);
     if (r) return r;
     s->b->state_set = true;
+    s->b->sigma_pending = sigma_x == nullptr;
     return post_set(s->b, sigma_x == nullptr);
 }
 
@@ -701,6 +706,7 @@ int cgks_set_state_device(cgks_solver* s, const double* W, const double* Wx, con
     int r = set_state_impl(s->b, 0, W, Wx, Wy, Wx_line, Wy_line, sigma_x, sigma_y, cudaMemcpyDeviceToDevice, false);
     if (r) return r;
     s->b->state_set = true;
+    s->b->sigma_pending = sigma_x == nullptr;
     if ((r = convert_state(s->b, 1))) return r;
     if (sigma_x == nullptr) return launch(s->b, (const void*)s->b->k.siginit, W_SIGINIT, 6, 0, false);
     return CGKS_OK;
@@ -719,6 +725,9 @@ int cgks_set_time(cgks_solver* s, double t)
     cgks_batch* b = s->b;
     CK(cudaMemcpyAsync(b->host[0].t, &t, 8, cudaMemcpyHostToDevice, b->stream));
     CK(cudaMemcpyAsync(b->host[0].tn, &t, 8, cudaMemcpyHostToDevice, b->stream));
+    // a sigma that set_state initialised from the cell averages takes the
+    // ghost states of inflow sides at this time, as if the state had been set at t
+    if (b->sigma_pending) return launch(b, (const void*)b->k.siginit, W_SIGINIT, 6, 0, false);
     return CGKS_OK;
 }
 
@@ -751,6 +760,7 @@ int cgks_advance(cgks_solver* s, int n, double dt)
     int which = dt > 0.0 ? 0 : 1;
     int r = build_graph(b, which);
     if (r) return r;
+    if (n > 0) b->sigma_pending = false;
     for (int q = 0; q < n; ++q) {
         if (which == 0) {
             CK(cudaMemcpyAsync(b->dfixed, &dt, 8, cudaMemcpyHostToDevice, b->stream));
@@ -932,6 +942,27 @@ int cgks_batch_set_state(cgks_batch* b, int k, const double* W, const double* Wx
     return post_set_one(b, k);
 }
 
+int cgks_batch_set_state_device(cgks_batch* b, int k, const double* W, const double* Wx, const double* Wy,
+                                const double* Wx_line, const double* Wy_line)
+{
+    if (!b) return CGKS_EINVAL;
+    int r = set_state_impl(b, k, W, Wx, Wy, Wx_line, Wy_line, nullptr, nullptr, cudaMemcpyDeviceToDevice, false);
+    if (r) return r;
+    b->state_set = true;
+    // the float planes, sigma from the cell averages and the positivity check of
+    // instance k, enqueued; a non-physical state shows in cgks_batch_sync
+    if (b->rsize == 4 && (r = launch_one(b, k, (const void*)b->k.convert, W_CELLS, 1, true))) return r;
+    if ((r = launch_one(b, k, (const void*)b->k.siginit, W_SIGINIT, 0, false))) return r;
+    return launch_one(b, k, (const void*)b->k.check, W_CELLS, 0, false);
+}
+
+int cgks_batch_get_state_device(cgks_batch* b, int k, double* W, double* Wx, double* Wy, double* Wx_line,
+                                double* Wy_line)
+{
+    if (!b) return CGKS_EINVAL;
+    return get_state_impl(b, k, W, Wx, Wy, Wx_line, Wy_line, nullptr, nullptr, cudaMemcpyDeviceToDevice, false);
+}
+
 int cgks_batch_step(cgks_batch* b, const double* dt)
 {
     if (!b || !b->state_set) return CGKS_EINVAL;
@@ -993,12 +1024,14 @@ namespace {
 
 const int kMaxDevices = 64;
 unsigned char* g_noalloc_base[kMaxDevices];  // device address of the array, per device
+std::mutex g_noalloc_mu;                     // host threads racing on a first call set up once
 
 // Once per device, with that device current: the array's device address
 // (host code must not use the array's name as an address) and the tables.
 int noalloc_setup(int dev)
 {
     if (dev < 0 || dev >= kMaxDevices) return CGKS_ENOTSUP;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (g_noalloc_base[dev]) return CGKS_OK;
     void* ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return CGKS_ECUDA;
@@ -1006,6 +1039,26 @@ int noalloc_setup(int dev)
     if (r) return r;
     g_noalloc_base[dev] = (unsigned char*)ptr;
     return CGKS_OK;
+}
+
+// Everything a no-allocation step must place in the array before its stage
+// kernels run, passed by value: kernel arguments are copied when the launch
+// is enqueued, so no host memory is read later.
+struct NoallocInit {
+    Mesh g;
+    long long off[W_COUNT * 2];
+    double dt;  // > 0: the fixed step
+};
+static_assert(sizeof(NoallocInit) <= 4000, "kernel arguments are limited to 4 KB");
+
+__global__ void k_noalloc_init(NoallocInit a, Mesh* dmesh, long long* doff, unsigned long long* scal)
+{
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int q = 0; q < 64; ++q) scal[q] = 0ull;  // the 512 bytes of scalars
+    *dmesh = a.g;
+    for (int q = 0; q < W_COUNT * 2; ++q) doff[q] = a.off[q];
+    *a.g.bad = LLONG_MAX;
+    if (a.dt > 0.0) *a.g.dt = a.dt;
 }
 
 } // namespace
@@ -1068,20 +1121,24 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     g.bad = (long long*)(sc + 24); g.smax = (unsigned long long*)(sc + 32);
     g.branch = (unsigned long long*)(sc + 40); g.dtf = (float*)(sc + 72); g.ghost = (const double*)(sc + 80);
     g.tn = (double*)(sc + 368); g.nfall = (unsigned long long*)(sc + 376);
-    long long off[W_COUNT * 2];
-    for (int kind = 0; kind < W_COUNT; ++kind) { off[2 * kind] = 0; off[2 * kind + 1] = items(kind, 1, 1, nx, 1); }
+    NoallocInit init;
+    std::memset(&init, 0, sizeof(init));
+    init.g = g;
+    const long long* off = init.off;
+    for (int kind = 0; kind < W_COUNT; ++kind) { init.off[2 * kind] = 0; init.off[2 * kind + 1] = items(kind, 1, 1, nx, 1); }
+    init.dt = dt;
     Mesh* dmesh = (Mesh*)(base + oM);
     long long* doff = (long long*)(base + oOF);
-    // scalars start from zero (bad index from its maximum); descriptor and offsets in
-    CK(cudaMemsetAsync(sc, 0, 512, st));
-    long long mx = LLONG_MAX;
-    CK(cudaMemcpyAsync(g.bad, &mx, 8, cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(dmesh, &g, sizeof(Mesh), cudaMemcpyHostToDevice, st));
-    CK(cudaMemcpyAsync(doff, off, sizeof(off), cudaMemcpyHostToDevice, st));
+    // scalars start from zero (bad index from its maximum); descriptor, offsets
+    // and the fixed step in, all as kernel arguments
+    {
+        unsigned long long* scal = (unsigned long long*)sc;
+        void* args[] = {&init, &dmesh, &doff, &scal};
+        CK(cudaLaunchKernel((const void*)k_noalloc_init, dim3(1), dim3(32), args, 0, st));
+    }
     if (state_out != state_in) CK(cudaMemcpyAsync(state_out, state_in, 6 * (size_t)nx * 8, cudaMemcpyDeviceToDevice, st));
     if (sigma_in && sigma_in != sigma_out)
         CK(cudaMemcpyAsync(sigma_out, sigma_in, (size_t)(nx + 1) * 8, cudaMemcpyDeviceToDevice, st));
-    if (dt > 0.0) CK(cudaMemcpyAsync(g.dt + 0, &dt, 8, cudaMemcpyHostToDevice, st));
     Kfns k = pick_kfns(1, p->order, p->precision, p->tau_mode, p->bc, p->pt_fallback);
     int nsm = 1;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));

@@ -85,3 +85,36 @@ def test_batch_instance_matches_oracle():
         for f, ref in (("Wx_line", o.Wxl), ("Wy_line", o.Wyl)):
             d = np.abs(g[f] - ref).sum()
             assert d <= 1e-12 * np.abs(ref).sum() + ref.size * floor, (k, f, d)
+
+
+def test_batch_device_state_calls_equal_host_calls():
+    """cgks_batch_set_state_device / _get_state_device (CUDA tensors, enqueued
+    on the batch's stream) give bitwise the same steps as the host-array calls,
+    in both precision forms."""
+    import torch
+    sp = specs(4, seed=9)
+    order = 5
+    states = [inputs.batch_instance(s, order) for s in sp]
+    names = ("W", "Wx", "Wy", "Wx_line", "Wy_line")
+    for precision in (cgks.FP64, cgks.FP32_BULK):
+        args = ([s["nx"] for s in sp], [s["ny"] for s in sp], [ext_of(s) for s in sp])
+        bh = cgks.Batch(order, *args, precision=precision, tau_mode=cgks.TAU_HGKS)
+        bd = cgks.Batch(order, *args, precision=precision, tau_mode=cgks.TAU_HGKS,
+                        stream=torch.cuda.current_stream().cuda_stream)
+        for k, st in enumerate(states):
+            bh.set_state(k, *st)
+            bd.set_state_device(k, *[torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in st])
+        for _ in range(2):
+            bh.step(None)
+            bd.step(None)
+        bh.sync()
+        bd.sync()
+        for k, st in enumerate(states):
+            out = {n: torch.empty(a.shape, dtype=torch.float64, device="cuda") for n, a in zip(names, st)}
+            bd.get_state_device(k, out)
+            torch.cuda.synchronize()
+            gh = bh.get_state(k)
+            for n in names:
+                assert np.array_equal(out[n].cpu().numpy(), gh[n]), (precision, k, n)
+        bh.close()
+        bd.close()
