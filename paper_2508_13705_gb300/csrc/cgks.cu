@@ -253,9 +253,11 @@ Layout layout(int dim, int M, size_t rs, int nx, int ny)
     size_t plane = (size_t)nx * ny;
     int np = dim == 2 ? 12 + 8 * M : 6;
     int nacc = dim == 2 ? 4 + 8 * M : 6;
+    int nv = dim + 2;
     size_t o = 0;
     L.S = o; o = align256(o + 2 * np * plane * 8);
-    L.F = o; o = align256(o + (rs == 4 ? 2 * np * plane * 4 : 0));  // FP32-bulk float planes
+    // FP32-bulk float planes: every state plane plus the low parts of the averages
+    L.F = o; o = align256(o + (rs == 4 ? 2 * (np + nv) * plane * 4 : 0));
     L.ACC = o; o = align256(o + nacc * plane * 8);
     L.sigx = o; o = align256(o + 2 * (size_t)(nx + 1) * ny * 8);
     L.sigy = o; o = align256(o + (dim == 2 ? 2 * (size_t)(ny + 1) * nx * 8 : 0));
@@ -351,7 +353,7 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         g.S1 = g.S0 + (size_t)b->nplanes * g.plane;
         if (b->rsize == 4) {
             g.F0 = (float*)(m0 + L[k].F);
-            g.F1 = g.F0 + (size_t)b->nplanes * g.plane;
+            g.F1 = g.F0 + (size_t)(b->nplanes + b->nvar) * g.plane;
         }
         g.ACC = (double*)(m0 + L[k].ACC);
         g.sig_x = (double*)(m0 + L[k].sigx);
@@ -1087,7 +1089,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     size_t oFR = take(3 * (size_t)(nx + 1) * 24 * rs), oFO = take((size_t)(nx + 1) * 16 * rs);
     size_t oSP = take((size_t)(nx + 1) * 8), oSC = take(512), oM = take(sizeof(Mesh));
     size_t oOF = take(W_COUNT * 2 * sizeof(long long));
-    size_t oF = take(rs == 4 ? 2 * 6 * (size_t)nx * 4 : 0);  // FP32-bulk float planes
+    size_t oF = take(rs == 4 ? 2 * 9 * (size_t)nx * 4 : 0);  // FP32-bulk float planes and low parts
     if (o > CGKS_NOALLOC_SCRATCH_BYTES) return CGKS_EINVAL;
     unsigned char* base = g_noalloc_base[dev];
     Mesh g;
@@ -1110,7 +1112,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     g.S1 = (double*)(base + oS1);
     if (rs == 4) {
         g.F0 = (float*)(base + oF);
-        g.F1 = g.F0 + 6 * (size_t)nx;
+        g.F1 = g.F0 + 9 * (size_t)nx;
     }
     g.ACC = (double*)(base + oACC);
     g.sig_x = sigma_out;

@@ -77,9 +77,10 @@ struct Mesh {
     // state: planes of nx*ny doubles.  2-D: W[4] Wx[4] Wy[4] Wxl[m][4] Wyl[m][4];
     // 1-D: W[3] Wx[3]
     double *S0, *S1;                // S0: state n (and n+1), S1: stage-1 state W*
-    float *F0, *F1;                 // FP32-bulk form: float copies of all planes of S0 / S1
-                                    // (the FP64 planes hold the cell averages; their
-                                    // slope planes are rebuilt from these on read-out)
+    float *F0, *F1;                 // FP32-bulk form: float copies of all planes of S0 / S1,
+                                    // then the low parts float(W - float(W)) of the cell
+                                    // averages (the FP64 planes hold the cell averages;
+                                    // their slope planes are rebuilt from these on read-out)
     double *ACC;                    // 2-D: W[4] Wxl[m][4] Wyl[m][4]; 1-D: W[3] Wface[3]
     double *sig_x, *sig_y;          // sigma of the previous step [ny][nx+1], [ny+1][nx]
     double *sig_xn, *sig_yn;        // sigma being built this step
@@ -185,7 +186,21 @@ __device__ __forceinline__ bool wall_flip(int kind, int v, int normal, int bc)
     return rev != dnormal;
 }
 
-// kind: 0 W, 1 Wx, 2 Wy, 3 Wx_line, 4 Wy_line (global orientation); tb: the
+// The low part of a cell average in the FP32-bulk form: the FP64 average x is
+// held as hi = float(x) (the W planes) plus lo = float(x - hi) (the planes
+// after all others); FP64 planes need no low part.
+template <typename T> __device__ __forceinline__ T low_part(double x) { return (T)(x - (double)(T)x); }
+template <> __device__ __forceinline__ double low_part<double>(double) { return 0.0; }
+
+// A prescribed ghost value x (fixed ghost cells, inflow states) as kind asks:
+// the value (kind 0), its low part (kind 5), or a zero slope.
+template <typename T> __device__ __forceinline__ T prescribed(double x, int kind)
+{
+    return kind == 0 ? (T)x : (kind == 5 ? low_part<T>(x) : (T)0);
+}
+
+// kind: 0 W, 1 Wx, 2 Wy, 3 Wx_line, 4 Wy_line (global orientation), 5 the low
+// part of W (FP32-bulk float planes only); tb: the
 // stage's time, read by inflow sides only.  Ghost rules apply x first, then y.
 // WALLS = false compiles the wall and inflow branches out: the stencil kernels
 // have an instance for meshes without them, whose hot loops the (never
@@ -201,10 +216,11 @@ __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, in
             i = imod(i, g.nx);
         } else if (bc == BC_FIXED) {
             int layer = side == 0 ? (-1 - i) : (i - g.nx);
-            return (T)g.ghost[((side * 3 + layer) * 2 + (kind == 0 ? 0 : 1)) * 3 + v];
+            double gv = g.ghost[((side * 3 + layer) * 2 + (kind == 0 || kind == 5 ? 0 : 1)) * 3 + v];
+            return kind == 5 ? low_part<T>(gv) : (T)gv;
         } else if (WALLS && (bc == BC_INFLOW || (bc == BC_INFLOW_REFLECTIVE && below_split(g, side, j, tb)))) {
             // prescribed state by the row's centre, zero slopes
-            return kind == 0 ? (T)g.bcs[side][below_split(g, side, j, tb) ? 0 : 1][v] : (T)0;
+            return prescribed<T>(g.bcs[side][below_split(g, side, j, tb) ? 0 : 1][v], kind);
         } else if (WALLS && is_mirror(bc)) {
             // ghost cell -1-k mirrors cell k; lines across x (Wy_line) swap ends
             i = i < 0 ? -1 - i : 2 * g.nx - 1 - i;
@@ -220,7 +236,7 @@ __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, in
         int bc = g.bc[side];
         if (WALLS && (bc == BC_INFLOW || (bc == BC_INFLOW_REFLECTIVE && below_split(g, side, i, tb)))) {
             // prescribed state by the column's centre (after the x rule), zero slopes
-            T val = kind == 0 ? (T)g.bcs[side][below_split(g, side, i, tb) ? 0 : 1][v] : (T)0;
+            T val = prescribed<T>(g.bcs[side][below_split(g, side, i, tb) ? 0 : 1][v], kind);
             return neg ? -val : val;
         }
         if (bc == BC_PERIODIC) {
@@ -238,13 +254,14 @@ __device__ __forceinline__ T cell(const Mesh& g, const T* S, int kind, int v, in
     long long idx = (long long)j * g.nx + i;
     int p;
     if (D == 1) {
-        p = kind == 0 ? v : 3 + v;
+        p = kind == 0 ? v : (kind == 5 ? 6 + v : 3 + v);
     } else {
         switch (kind) {
         case 0: p = v; break;
         case 1: p = 4 + v; break;
         case 2: p = 8 + v; break;
         case 3: p = 12 + 4 * l + v; break;
+        case 5: p = 12 + 8 * M + v; break;
         default: p = 12 + 4 * M + 4 * l + v; break;
         }
     }
@@ -309,6 +326,89 @@ __device__ __forceinline__ void st4(double* p, const double v[4])
 {
     *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
     *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+}
+
+// ------------------------------------------------------------------ float-float
+// Unevaluated sums hi + lo of two floats (Dekker's double-length arithmetic,
+// with Knuth's two-sum and the FMA two-product), about 44 significant bits:
+// FP64-level accuracy from FP32 instructions, for the few O(1) quantities of
+// the FP32-bulk form whose rounding would otherwise enter every update.  The
+// explicit _rn intrinsics keep the compiler from contracting or reassociating.
+struct ff { float hi, lo; };
+
+__device__ __forceinline__ ff ff_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ ff ff_norm(float hi, float lo)  // |hi| >= |lo|
+{
+    float s = __fadd_rn(hi, lo);
+    return {s, __fsub_rn(lo, __fsub_rn(s, hi))};
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    ff s = ff_two_sum(a.hi, b.hi);
+    return ff_norm(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+    return ff_norm(p, e);
+}
+__device__ __forceinline__ ff ff_of(float a) { return {a, 0.0f}; }
+// a / b of two floats: the remainder a - q b of the rounded quotient is exact
+__device__ __forceinline__ ff ff_div(float a, float b)
+{
+    float q = __fdiv_rn(a, b);
+    return ff_norm(q, __fdiv_rn(__fmaf_rn(-q, b, a), b));
+}
+__device__ __forceinline__ double ff_val(ff a) { return (double)a.hi + (double)a.lo; }
+
+// Euler flux along the local normal of a state given by floats (rho, m_n,
+// m_t, E) (2-D, D = 2) or (rho, m, E) (1-D), in float-float: (m_n, m_n u + p,
+// m_t u, u (E + p)) with u = m_n / rho, p = (gamma - 1)(E - (m_n u + m_t v) / 2).
+// gm1 = gamma - 1 as a float-float.
+template <int D>
+__device__ __forceinline__ void euler_flux_ff(const float* w, ff gm1, double* F)
+{
+    const float rho = w[0], mn = w[1], mt = D == 2 ? w[2] : 0.0f, E = w[D + 1];
+    ff u = ff_div(mn, rho);
+    ff v = ff_div(mt, rho);
+    ff ke = ff_add(ff_mul(ff_of(mn), u), ff_mul(ff_of(mt), v));  // rho |U|^2
+    ff p = ff_mul(gm1, ff_add(ff_of(E), ff_mul(ff_of(-0.5f), ke)));
+    F[0] = (double)mn;
+    F[1] = ff_val(ff_add(ff_mul(ff_of(mn), u), p));
+    if (D == 2) F[2] = ff_val(ff_mul(ff_of(mt), u));
+    F[D + 1] = ff_val(ff_mul(u, ff_add(ff_of(E), p)));
+}
+
+// F(w0 + q) - F(w0) of the Euler flux along the local normal, by algebra in
+// which every term is a product with a component of q (no difference of two
+// O(1) values), so the result keeps the relative accuracy of q.  w0: the base
+// state (floats), q: the increment; same layouts as euler_flux_ff.
+template <int D, typename R>
+__device__ __forceinline__ void euler_flux_delta(const R* w0, const R* q, R gm1, R* dF)
+{
+    const R r0 = w0[0], mn0 = w0[1], mt0 = D == 2 ? w0[2] : (R)0, E0 = w0[D + 1];
+    const R dr = q[0], dmn = q[1], dmt = D == 2 ? q[2] : (R)0, dE = q[D + 1];
+    const R ir0 = (R)1 / r0;
+    const R u0 = mn0 * ir0, v0 = mt0 * ir0;
+    const R ir = (R)1 / (r0 + dr);
+    const R du = (dmn - u0 * dr) * ir, dv = (dmt - v0 * dr) * ir;  // u - u0, v - v0
+    const R u = u0 + du;
+    // kinetic energy rho |U|^2 / 2: its change, product by product
+    const R dke = (R)0.5 * (dr * (u0 * u0 + v0 * v0) + (r0 + dr) * (du * ((R)2 * u0 + du) + dv * ((R)2 * v0 + dv)));
+    const R p0 = gm1 * (E0 - (R)0.5 * r0 * (u0 * u0 + v0 * v0));
+    const R dp = gm1 * (dE - dke);
+    dF[0] = dmn;
+    dF[1] = dmn * u + mn0 * du + dp;             // (m u + p) - (m0 u0 + p0)
+    if (D == 2) dF[2] = dmt * u + mt0 * du;      // m_t u - m_t0 u0
+    dF[D + 1] = du * (E0 + p0) + u * (dE + dp);  // u H - u0 H0, H = E + p
 }
 
 // ------------------------------------------------------------------ ASE-DFF

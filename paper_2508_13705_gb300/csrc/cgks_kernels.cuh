@@ -10,6 +10,8 @@
 // normal; M Gauss points per face).  Direction 0 as written; direction 1 with
 // the two spatial indices swapped, so the global x index is always fastest:
 //   LA  [M][nb+2][na+6][4]            line averages, b in [-1, nb], a in [-3, na+2]
+//                                     (FP32-bulk form: the line average minus the
+//                                     high part hi of the cell average, see below)
 //   FR  [2]{[nb+2][na+1][M][8], [nb+2][na+1][M][4]}
 //                                     face states: side 0 = left (from cell f-1),
 //                                     side 1 = right (from cell f); per side one
@@ -20,6 +22,19 @@
 //   SP  [nb][na+1][M]                 sigma per face Gauss point (Eq. 3.2)
 //   AT  [nb+2][na+6]                  tangential r5 DFF of each cell (Step 3)
 //   DN  [nb+2][na+6][4]               normal-direction DFF of each cell (Step 2), packed
+//
+// FP32-bulk form: a cell average W (FP64) is held in the float planes as
+// hi = float(W) and lo = float(W - hi), and every reconstructed quantity that
+// is a value (line averages, face states, the equilibrium state, the
+// interface states) is carried as an increment over the hi of one cell: the
+// line average of cell i as lo_i + (its reconstruction's increment), a face
+// state of cell i as an increment over hi_i, the face's equilibrium state and
+// interface states as increments over hi of the face's right cell.  Stencil
+// data enter as differences (hi_k - hi_i) + (lo_k - lo_i), exact in float
+// for neighbouring values, so the FP32 arithmetic only ever rounds small
+// increments; the O(1) Euler flux of the base hi is formed in float-float in
+// the update and the flux of the increment by difference algebra in the
+// flux kernel.  The rounding that remains is relative to the increments.
 #pragma once
 #include "cgks_device.cuh"
 
@@ -34,13 +49,14 @@ __device__ __forceinline__ void local_dims(const Mesh& g, int dir, int& na, int&
     nb = dir == 0 ? g.ny : g.nx;
 }
 
-// cell value in local coordinates; lkind: 0 W, 1 W_n (cell), 2 W_t (cell), 3 W_n line
+// cell value in local coordinates; lkind: 0 W, 1 W_n (cell), 2 W_t (cell), 3 W_n line,
+// 5 the low part of W (FP32-bulk form)
 template <int D, int M, typename T, bool WALLS = true>
 __device__ __forceinline__ T lcell(const Mesh& g, const T* S, int dir, int lkind, int v, int l, int a, int b,
                                    double tb)
 {
     int kind;
-    if (lkind == 0) kind = 0;
+    if (lkind == 0 || lkind == 5) kind = lkind;  // W, or its low part (FP32-bulk form)
     else if (lkind == 1) kind = dir == 0 ? 1 : 2;
     else if (lkind == 2) kind = dir == 0 ? 2 : 1;
     else kind = dir == 0 ? 3 : 4;
@@ -129,17 +145,20 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         long long ci = dir == 0 ? (long long)b * g.nx + a : (long long)a * g.nx + b;
         long long st = dir == 0 ? g.nx : 1;  // tangential neighbour stride
         int pt = dir == 0 ? 8 : 4;           // plane of the tangential cell slope
-        R sw[4][5], swt[4][5];
+        constexpr bool BULK32 = sizeof(R) == 4;
+        R sw[4][5], swt[4][5], slo[4][BULK32 ? 5 : 1];  // slo: low parts of the averages (FP32 bulk)
         if (inner) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
                 int gv = vglob(dir, v);
                 const R* w0 = S + gv * P + ci;
                 const R* wt = S + (pt + gv) * P + ci;
+                const R* wl = S + (12 + 8 * M + gv) * P + ci;
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
                     sw[v][q] = w0[(q - 2) * st];
                     swt[v][q] = wt[(q - 2) * st];
+                    if (BULK32) slo[v][BULK32 ? q : 0] = wl[(q - 2) * st];
                 }
             }
         } else {
@@ -149,6 +168,7 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
                 for (int q = 0; q < 5; ++q) {
                     sw[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 0, v, 0, a, b + q - 2, tb);
                     swt[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 2, v, 0, a, b + q - 2, tb);
+                    if (BULK32) slo[v][BULK32 ? q : 0] = lcell<2, M, R, WALLS>(g, S, dir, 5, v, 0, a, b + q - 2, tb);
                 }
         }
         // face sigma of the tangential stencil: a direct walk for interior cells
@@ -193,16 +213,19 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
             constexpr int ST = decltype(tag)::value;
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
+                // FP32 bulk: differences of averages as (hi - hi) + (lo - lo), and
+                // the line average kept as lo + increment (over the cell's hi)
                 R qi = sw[v][2], dp[10];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
-                    dp[q] = sw[v][q] - qi;
+                    dp[q] = BULK32 ? (sw[v][q] - qi) + (slo[v][BULK32 ? q : 0] - slo[v][BULK32 ? 2 : 0]) : sw[v][q] - qi;
                     dp[5 + q] = ht * swt[v][q];
                 }
                 R out[M];
                 recon_st<R, M, M - 2, ST, 6>(dff, dp, out, ghi, glo, eps);
+                const R base = BULK32 ? slo[v][BULK32 ? 2 : 0] : qi;
 #pragma unroll
-                for (int l = 0; l < M; ++l) res[l][v] = qi + out[l];
+                for (int l = 0; l < M; ++l) res[l][v] = base + out[l];
             }
         });
 #pragma unroll
@@ -219,6 +242,7 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
     if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
     __syncthreads();
     constexpr int NV = D + 2;
+    constexpr bool BULK32 = sizeof(R) == 4;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
          gi += (long long)gridDim.x * blockDim.x) {
         int k = find_mesh(w, gi);
@@ -281,19 +305,29 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         // all line slopes of the stencil are loaded before the first
         // reconstruction, so their latencies overlap
         R sl[D == 2 ? NV : 1][5];
+        // FP32 bulk: the high parts of the five cell averages along the normal,
+        // whose differences join those of the line averages' increments
+        R sh[D == 2 && BULK32 ? NV : 1][5];
         if (D == 2) {
             if (inner) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
                     const R* ws = S + (pl0 + vglob(dir, v)) * P + ci;
+                    const R* wh = S + vglob(dir, v) * P + ci;
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) sl[v][q] = ws[(q - 2) * sn];
+                    for (int q = 0; q < 5; ++q) {
+                        sl[v][q] = ws[(q - 2) * sn];
+                        if (BULK32) sh[BULK32 ? v : 0][q] = wh[(q - 2) * sn];
+                    }
                 }
             } else {
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) sl[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 3, v, l, a + q - 2, b, tb);
+                    for (int q = 0; q < 5; ++q) {
+                        sl[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 3, v, l, a + q - 2, b, tb);
+                        if (BULK32) sh[BULK32 ? v : 0][q] = lcell<2, M, R, WALLS>(g, S, dir, 0, v, 0, a + q - 2, b, tb);
+                    }
             }
         }
         const R ghi = (R)g.ghi, glo = (R)g.glo, eps = (R)g.eps;
@@ -303,10 +337,13 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
                 constexpr int ST = decltype(tag)::value;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
+                    // FP32 bulk: la5 holds increments over the cells' hi, so a
+                    // difference of line averages is (hi - hi) + (la - la), and the
+                    // face values come out as increments over this cell's hi
                     R qi = la5[2][v], dp[10];
 #pragma unroll
                     for (int q = 0; q < 5; ++q) {
-                        dp[q] = la5[q][v] - qi;
+                        dp[q] = BULK32 ? (sh[BULK32 ? v : 0][q] - sh[BULK32 ? v : 0][2]) + (la5[q][v] - qi) : la5[q][v] - qi;
                         dp[5 + q] = hn * sl[v][q];
                     }
                     R out[6];
@@ -318,13 +355,18 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
         } else {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
+                // FP32 bulk: differences as (hi - hi) + (lo - lo); the face values
+                // come out as increments over this cell's hi (qi = lo)
                 R qi = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a, 0, tb);
+                R ql = BULK32 ? cell<1, 1, R, WALLS>(g, S, 5, v, 0, a, 0, tb) : (R)0;
                 R dp[10];
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
                     dp[q] = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a + q - 2, 0, tb) - qi;
+                    if (BULK32) dp[q] += cell<1, 1, R, WALLS>(g, S, 5, v, 0, a + q - 2, 0, tb) - ql;
                     dp[5 + q] = hn * cell<1, 1, R, WALLS>(g, S, 1, v, 0, a + q - 2, 0, tb);
                 }
+                if (BULK32) qi = ql;
                 R out[6];
                 recon<R, 6>(dff, g.oi, 0, dp, out, ghi, glo, eps);
                 sideL[0][v] = qi + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
@@ -370,15 +412,26 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
 {
     constexpr int NV = D + 2;
     constexpr int ND = D == 2 ? 5 : 2;  // derivatives: n, nn (, t, tt, nt)
+    constexpr bool BULK32 = sizeof(R) == 4;
     // Step 3 weights in shared memory: the Gauss line differs across the lanes
-    // of a warp, which would serialise constant-memory reads
+    // of a warp, which would serialise constant-memory reads.  FP32 bulk also
+    // keeps, per line and segment, the sum of the segment's weights, which
+    // multiplies the difference of the segment cell's hi from the centre's.
     __shared__ R s_d1[4][12], s_d2[4][12];
+    __shared__ R s_c1[4][3], s_c2[4][3];
     if (D == 2) {
         const auto& T = Tab<R>::get(w.mesh[0].oi);  // a table shares one order
         for (int q = threadIdx.x; q < 48; q += blockDim.x) {
             s_d1[q / 12][q % 12] = T.d1[q / 12][q % 12];
             s_d2[q / 12][q % 12] = T.d2[q / 12][q % 12];
         }
+        if (BULK32)
+            for (int q = threadIdx.x; q < 12; q += blockDim.x) {
+                R c1 = 0, c2 = 0;
+                for (int kk = 0; kk < M; ++kk) { c1 += T.d1[q / 3][(q % 3) * M + kk]; c2 += T.d2[q / 3][(q % 3) * M + kk]; }
+                s_c1[q / 3][q % 3] = c1;
+                s_c2[q / 3][q % 3] = c2;
+            }
         __syncthreads();
     }
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
@@ -402,7 +455,44 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         const R* FR = (const R*)g.FR[dir];
         const R gm = MeshR<R>::gamma(g), K = MeshR<R>::K(g);
         constexpr bool hgks = HG != 0;  // the collision-time terms of Eq. 2.6 (tau > 0)
-        R e1[4] = {1, 0, 0, 0};
+        const long long npt = fr_npt(na, nb, M);
+        const long long p00 = fr_row(dir, na, nb, b, f) * M;
+        const long long rs = (dir == 0 ? (long long)(na + 1) : 1LL) * M;  // FR row stride of the segments
+        // FP32 bulk: the state planes of this stage, whose high parts hi are the
+        // bases of the face states (local frame); hi of cell (a, bb)
+        const R* SF = state_planes<R>(g, STAGE == 1 ? 0 : 1);
+        const double tb = stage_time(g, STAGE);
+        auto hi_of = [&](int a, int bb, R out[4]) {
+            if (a >= 0 && a < na && bb >= 0 && bb < nb) {
+                long long ci = dir == 0 ? (long long)bb * g.nx + a : (long long)a * g.nx + bb;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) out[v] = SF[vglob(dir, v) * g.plane + ci];
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) out[v] = lcell<D, M, R, true>(g, SF, dir, 0, v, 0, a, bb, tb);
+            }
+            if (NV < 4) out[3] = (R)0;
+        };
+        // W_l - W_r from differences of hi and of the increments, and whether it
+        // is small enough for the kinetic weighting to be taken to first order
+        // in it (below); hb1: hi of the right cell f, the base of the face
+        R hb1[4], dW[4] = {0, 0, 0, 0}, Dl[4] = {0, 0, 0, 0};
+        bool lin = false;
+        if (BULK32) {
+            R hb0[4], e0[4], e1[4];
+            hi_of(f - 1, b, hb0);
+            hi_of(f, b, hb1);
+            ld4(FR + (p00 + rs + l) * 8, e0);
+            ld4(FR + npt * 12 + (p00 + rs + l) * 8, e1);
+            R sc = fabs(hb1[0]) + fabs(hb1[NV - 1]);
+            lin = true;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                dW[v] = (hb0[v] - hb1[v]) + (e0[v] - e1[v]);
+                lin &= fabs(dW[v]) <= (R)2.5e-4 * sc;
+            }
+        }
+        R e1v[4] = {1, 0, 0, 0};
         R Q0[4] = {0, 0, 0, 0};
         R dQ[ND][4];
 #pragma unroll
@@ -414,14 +504,12 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         bool bad = false, ok = true;
 #pragma unroll 1
         for (int side = 0; side < 2; ++side) {
-            // Step 2 data: W, W_n, W_nn
+            // Step 2 data: W, W_n, W_nn (FP32 bulk: W as an increment over hb)
             R d[6][4];
-            // this side's W plane and the row stride of the tangential segments
-            // (FR point of segment b + s, line kk: p00 + s * rs + kk)
-            const long long npt = fr_npt(na, nb, M);
-            const long long p00 = fr_row(dir, na, nb, b, f) * M;
-            const R* Fs = FR + side * npt * 12 + p00 * 8;                 // (W, W_n) of segment b - 1
-            const long long rs = (dir == 0 ? (long long)(na + 1) : 1LL) * M;
+            const int a = side == 0 ? f - 1 : f;  // the reconstructing cell
+            R hb[4] = {0, 0, 0, 0};
+            if (BULK32) hi_of(a, b, hb);
+            const R* Fs = FR + side * npt * 12 + p00 * 8;  // (W, W_n) of segment b - 1
             ld4(Fs + (rs + l) * 8, d[0]);
             ld4(Fs + (rs + l) * 8 + 4, d[1]);
             ld4(FR + side * npt * 12 + npt * 8 + (p00 + rs + l) * 4, d[2]);
@@ -429,7 +517,6 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
                 // Step 3: tangential derivatives from the 3M face points of
                 // segments b-1, b, b+1, scaled by the tangential r5 DFF of the
                 // reconstructing cell (a = f-1 for the left state, f for the right)
-                int a = side == 0 ? f - 1 : f;
                 R at = ((const R*)g.AT[dir])[cell_idx(dir, na, nb, a, b)];
                 R iht = (R)1 / (R)(dir == 0 ? g.dy : g.dx);
                 R c1 = at * iht, c2 = at * iht * iht;
@@ -450,6 +537,20 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
                             wnt[v] += w1 * x1[v];
                         }
                     }
+                if (BULK32) {
+                    // the segment points' values are increments over the hi of
+                    // their own cells: add the bases' part, with the weights of
+                    // a constant summing to zero
+                    R hm[4], hp[4];
+                    hi_of(a, b - 1, hm);
+                    hi_of(a, b + 1, hp);
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        R dm = hm[v] - hb[v], dpl = hp[v] - hb[v];
+                        wt[v] += s_c1[l][0] * dm + s_c1[l][2] * dpl;
+                        wtt[v] += s_c2[l][0] * dm + s_c2[l][2] * dpl;
+                    }
+                }
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
                     d[3][v] = c1 * wt[v];
@@ -457,22 +558,29 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
                     d[5][v] = c1 * wnt[v];
                 }
             }
+            // the side's state
+            R ws[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) ws[v] = BULK32 ? hb[v] + d[0][v] : d[0][v];
             if (PF) {
                 // fallback: a side whose point state has rho <= 0 or p <= 0 takes
-                // the average of the cell it was reconstructed from, first order
-                R rho = d[0][0];
-                R m2 = d[0][1] * d[0][1] + (D == 2 ? d[0][2] * d[0][2] : (R)0);
-                R p = (gm - (R)1) * (d[0][NV - 1] - (R)0.5 * m2 / rho);
-                if (!(rho > (R)0) || !(p > (R)0)) {
-                    const R* S = state_planes<R>(g, STAGE == 1 ? 0 : 1);
-                    const double tb = stage_time(g, STAGE);
-                    int a = side == 0 ? f - 1 : f;
+                // the average of the cell it was reconstructed from, first order;
+                // the test is made in FP64 (FP32 bulk: on hi + increment)
+                double W4[4];
+#pragma unroll
+                for (int v = 0; v < 4; ++v) W4[v] = BULK32 ? (double)hb[v] + (double)d[0][v] : (double)d[0][v];
+                double rho = W4[0];
+                double m2 = W4[1] * W4[1] + (D == 2 ? W4[2] * W4[2] : 0.0);
+                double p = (g.gamma - 1.0) * (W4[NV - 1] - 0.5 * m2 / rho);
+                if (!(rho > 0.0) || !(p > 0.0)) {
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        d[0][v] = lcell<D, M, R, true>(g, S, dir, 0, v, 0, a, b, tb);
+                        d[0][v] = lcell<D, M, R, true>(g, SF, dir, BULK32 ? 5 : 0, v, 0, a, b, tb);
+                        ws[v] = BULK32 ? hb[v] + d[0][v] : d[0][v];
 #pragma unroll
                         for (int q = 1; q < 6; ++q) d[q][v] = (R)0;
                     }
+                    lin = false;  // the states changed: weight them directly
                     atomicAdd(g.nfall, 1ull);
                 }
             }
@@ -480,44 +588,69 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
             // states carry (the face means, stencil sums and branch thresholds
             // that use sigma are FP64)
             {
-                R rho = d[0][0];
+                R rho = ws[0];
                 R ir = (R)1 / rho;
-                R un = d[0][1] * ir;
-                R ut = D == 2 ? d[0][2] * ir : (R)0;
-                R p = (gm - (R)1) * (d[0][NV - 1] - (R)0.5 * rho * (un * un + ut * ut));
+                R un = ws[1] * ir;
+                R ut = D == 2 ? ws[2] * ir : (R)0;
+                R p = (gm - (R)1) * (ws[NV - 1] - (R)0.5 * rho * (un * un + ut * ut));
                 R ic = (R)1 / sqrt(gm * p * ir);
                 pz[side] = p; mn[side] = un * ic; mt[side] = ut * ic;
                 bad |= !(rho > (R)0) || !(p > (R)0);
             }
             // kinetic weighting (Eq. 2.7): this side's half-range integrals
             Mom<R, D> Ms;
-            ok &= maxwellian<R, D>(d[0], gm, K, side == 0 ? 1 : 2, Ms);
+            ok &= maxwellian<R, D>(ws, gm, K, side == 0 ? 1 : 2, Ms);
             Gram<R, D> Gs;  // half-range <psi psi> of this side
             gram<R, D, 0, 0>(Ms, Gs);
             R t[4], z[4];
             grow0<R, D>(Gs, Ms.rho, t);
 #pragma unroll
             for (int v = 0; v < NV; ++v) Q0[v] += t[v];
+            if (BULK32 && side == 0 && lin) {
+                // Q0 = W_r + (H(W_l) - H(W_r)), H the u > 0 half-range moments;
+                // for a small jump, H(W_l) - H(W_r) = dH/dW (W_l - W_r) to second
+                // order, where dH/dW dW = <psi a>_{u > 0} with <a> = dW: the
+                // rounding then stays relative to the jump
+                R aa[4];
+                slope<R, D>(Ms, K, dW, aa);
+                gmul<R, D>(Gs, aa, Ms.rho, Dl);
+            }
             if (hgks) {
-                mom<R, D>(Ms, e1, 1, 0, t);
+                mom<R, D>(Ms, e1v, 1, 0, t);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) T5[v] += Ms.rho * t[v];
             }
 #pragma unroll
             for (int q = 0; q < ND; ++q) {
-                R a[4];
-                slope<R, D>(Ms, K, d[q + 1], a);  // <a> = dW of this side (Eq. 2.8)
-                gmul<R, D>(Gs, a, Ms.rho, t);
+                R a_[4];
+                slope<R, D>(Ms, K, d[q + 1], a_);  // <a> = dW of this side (Eq. 2.8)
+                gmul<R, D>(Gs, a_, Ms.rho, t);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) dQ[q][v] += t[v];
                 if (hgks && (q == 0 || (D == 2 && q == 2))) {
                     // half-range (a_n u + a_t v) terms of Eq. 2.6, with and without the flux's u
                     int pu = q == 0 ? 1 : 0, pv = q == 0 ? 0 : 1;
-                    mom<R, D>(Ms, a, pu, pv, t);
-                    mom<R, D>(Ms, a, pu + 1, pv, z);
+                    mom<R, D>(Ms, a_, pu, pv, t);
+                    mom<R, D>(Ms, a_, pu + 1, pv, z);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) { S1h[v] += Ms.rho * t[v]; T6[v] += Ms.rho * z[v]; }
                 }
+            }
+        }
+        // FP32 bulk: the equilibrium state as an increment qv over hb1
+        R qv[4] = {0, 0, 0, 0};
+        if (BULK32) {
+            if (lin) {
+                R e1[4];
+                ld4(FR + npt * 12 + (p00 + rs + l) * 8, e1);
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    qv[v] = e1[v] + Dl[v];
+                    Q0[v] = hb1[v] + qv[v];
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) qv[v] = Q0[v] - hb1[v];
             }
         }
         double sig;
@@ -593,6 +726,15 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
             Wt[v] = -S1[v];
             Wtt[v] = -S2[v];
         }
+        // the flux carried out: F itself (FP64), or its increment over the Euler
+        // flux of hb1 (FP32 bulk; that flux is added in the update): the Euler
+        // flux of Q0 = hb1 + qv taken as a difference
+        R Fo[4];
+        if (BULK32) euler_flux_delta<D>(hb1, qv, gm - (R)1, Fo);
+        else {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Fo[v] = F[v];
+        }
         if (hgks) {
             // inviscid: c1 dt; viscous (Sec. 4): mu / p with p the pressure of
             // the equilibrium state at the face point
@@ -624,7 +766,8 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
             for (int v = 0; v < NV; ++v) {
                 R T3s = T3[v] * M0.rho, T4s = T4[v] * M0.rho, T2s = T2[v] * M0.rho;
                 R T0v = F[v], T1v = Ft[v];
-                F[v] = T0v * ((R)1 - f0) - tau * T1v + (f1 - tau) * T3s + f0 * T5[v] - f1 * T6[v];
+                // F = T0 + (the terms below); FP32 bulk adds them to the increment
+                Fo[v] += -f0 * T0v - tau * T1v + (f1 - tau) * T3s + f0 * T5[v] - f1 * T6[v];
                 Ft[v] = -g0 * T0v + T1v - tau * T2s + g1 * T3s - tau * T4s + g0 * T5[v] - g1 * T6[v];
                 R dS = S1[v] - S1h[v];
                 Wt[v] += ((R)2 * eh - ed) * dS;
@@ -640,11 +783,13 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         for (int v = 0; v < 4; ++v) {
             int gv = D == 2 ? vglob(dir, v) : v;
             if (v >= NV) { o[0][v] = o[1][v] = o[2][v] = o[3][v] = (R)0; continue; }
+            // interface-state values: Q0 itself, or its increment over hb1 (FP32 bulk)
+            const R Qv = BULK32 ? qv[v] : Q0[v];
             if (STAGE == 1) {
-                o[0][gv] = (R)0.5 * Dt * F[v] + (R)0.125 * Dt * Dt * Ft[v];
-                o[1][gv] = Dt * F[v] + Dt * Dt / (R)6 * Ft[v];
-                o[2][gv] = Q0[v] + (R)0.5 * Dt * Wt[v] + (R)0.125 * Dt * Dt * Wtt[v];
-                o[3][gv] = Q0[v] + Dt * Wt[v] + Dt * Dt / (R)6 * Wtt[v];
+                o[0][gv] = (R)0.5 * Dt * Fo[v] + (R)0.125 * Dt * Dt * Ft[v];
+                o[1][gv] = Dt * Fo[v] + Dt * Dt / (R)6 * Ft[v];
+                o[2][gv] = Qv + (R)0.5 * Dt * Wt[v] + (R)0.125 * Dt * Dt * Wtt[v];
+                o[3][gv] = Qv + Dt * Wt[v] + Dt * Dt / (R)6 * Wtt[v];
             } else {
                 o[0][gv] = Dt * Dt / (R)3 * Ft[v];
                 o[1][gv] = Dt * Dt / (R)3 * Wtt[v];
@@ -711,6 +856,41 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
         // face sums is taken exactly (exact_diff) into the FP64 averages, so
         // the updates telescope over the mesh and the totals change only by
         // the boundary fluxes and FP64 rounding.  Slopes use bulk differences.
+        // FP32 bulk, stage 1: the face outputs are increments over hi of each
+        // face's right cell (this cell for the left and bottom faces, cells
+        // (i+1, j) and (i, j+1) for the others).  Their flux parts add
+        // dt/2 (F(hi_R) - F(hi_L)) and dt (...) with the Euler fluxes F of the
+        // bases in float-float (each cell forms the same values bitwise, so
+        // the update still telescopes), their state parts the difference of
+        // the bases' hi.
+        R h0[4] = {0, 0, 0, 0}, hxn[4] = {0, 0, 0, 0}, hyn[4] = {0, 0, 0, 0};
+        double Bx[4] = {0, 0, 0, 0}, By[4] = {0, 0, 0, 0};
+        if (BULK32 && STAGE == 1) {
+            const float* SF = g.F0;
+            const double tb = *g.tn;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                h0[v] = (R)SF[v * P + c];
+                hxn[v] = (R)cell<2, M, float, true>(g, SF, 0, v, 0, i + 1, j, tb);
+                hyn[v] = (R)cell<2, M, float, true>(g, SF, 0, v, 0, i, j + 1, tb);
+            }
+            const double gm1d = g.gamma - 1.0;
+            const ff gm1 = {(float)gm1d, (float)(gm1d - (double)(float)gm1d)};
+            double f0[4], f1[4];
+            float wl[4];
+            // x: local frame = global (rho, m_x, m_y, E)
+            for (int v = 0; v < 4; ++v) wl[v] = (float)h0[v];
+            euler_flux_ff<2>(wl, gm1, f0);
+            for (int v = 0; v < 4; ++v) wl[v] = (float)hxn[v];
+            euler_flux_ff<2>(wl, gm1, f1);
+            for (int v = 0; v < 4; ++v) Bx[v] = f1[v] - f0[v];
+            // y: local frame (rho, m_y, m_x, E), back to global order
+            wl[0] = (float)h0[0]; wl[1] = (float)h0[2]; wl[2] = (float)h0[1]; wl[3] = (float)h0[3];
+            euler_flux_ff<2>(wl, gm1, f0);
+            wl[0] = (float)hyn[0]; wl[1] = (float)hyn[2]; wl[2] = (float)hyn[1]; wl[3] = (float)hyn[3];
+            euler_flux_ff<2>(wl, gm1, f1);
+            By[0] = f1[0] - f0[0]; By[1] = f1[2] - f0[2]; By[2] = f1[1] - f0[1]; By[3] = f1[3] - f0[3];
+        }
         R gxr0[4] = {0, 0, 0, 0}, gxl0[4] = {0, 0, 0, 0}, gyr0[4] = {0, 0, 0, 0}, gyl0[4] = {0, 0, 0, 0};
         R gxr1[4] = {0, 0, 0, 0}, gxl1[4] = {0, 0, 0, 0}, gyr1[4] = {0, 0, 0, 0}, gyl1[4] = {0, 0, 0, 0};
         R sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
@@ -730,6 +910,10 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
                 for (int v = 0; v < 4; ++v) {
                     R dx_ = a[v] - bq[v];
                     R dy_ = cq[v] - dq[v];
+                    if (BULK32 && STAGE == 1 && q >= 2) {  // interface states over the bases' hi
+                        dx_ += hxn[v] - h0[v];
+                        dy_ += hyn[v] - h0[v];
+                    }
                     if (q == 0) {
                         gxr0[v] += wl * a[v]; gxl0[v] += wl * bq[v];
                         gyr0[v] += wl * cq[v]; gyl0[v] += wl * dq[v];
@@ -765,8 +949,10 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
             const double dx0 = exact_diff(gxr0[v], gxl0[v]), dy0 = exact_diff(gyr0[v], gyl0[v]);
             if (STAGE == 1) {
                 double W = g.S0[v * P + c];
-                Wn = W - dx0 * idx - dy0 * idy;                                              // Eq. 2.21
-                g.ACC[v * P + c] = W - exact_diff(gxr1[v], gxl1[v]) * idx - exact_diff(gyr1[v], gyl1[v]) * idy;
+                const double dtd = *g.dt;
+                Wn = W - (dx0 + 0.5 * dtd * Bx[v]) * idx - (dy0 + 0.5 * dtd * By[v]) * idy;  // Eq. 2.21
+                g.ACC[v * P + c] = W - (exact_diff(gxr1[v], gxl1[v]) + dtd * Bx[v]) * idx
+                                     - (exact_diff(gyr1[v], gyl1[v]) + dtd * By[v]) * idy;
             } else {
                 Wn = g.ACC[v * P + c] - dx0 * idx - dy0 * idy;  // Eq. 2.22-2.23
             }
@@ -774,7 +960,9 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
             if (!BULK32 || STAGE == 2) out[v * P + c] = Wn;
             bad |= !isfinite(Wn);
             if (BULK32) {
-                outf[v * P + c] = (float)Wn;
+                const float hi = (float)Wn;
+                outf[v * P + c] = hi;
+                outf[(12 + 8 * M + v) * P + c] = (float)(Wn - (double)hi);  // low part
                 outf[(4 + v) * P + c] = (float)sx[v];  // cell slopes: Gauss sum of the line slopes
                 outf[(8 + v) * P + c] = (float)sy[v];
             } else {
@@ -830,15 +1018,35 @@ __global__ void __launch_bounds__(256) k_update1(Work w)
         const double idx = g.idx;
         long long P = g.plane;
         bool bad = false;
+        // FP32 bulk, stage 1: face outputs are increments over hi of the face's
+        // right cell (i, and i+1); their flux parts add the float-float Euler
+        // fluxes of the bases, their state parts the bases' difference
+        double B[3] = {0, 0, 0}, hd[3] = {0, 0, 0};
+        if (BULK32 && STAGE == 1) {
+            const double tb = *g.tn;
+            float h0[3], h1[3];
+            for (int v = 0; v < 3; ++v) {
+                h0[v] = g.F0[v * P + i];
+                h1[v] = cell<1, 1, float, true>(g, g.F0, 0, v, 0, i + 1, 0, tb);
+                hd[v] = (double)(h1[v] - h0[v]);
+            }
+            const double gm1d = g.gamma - 1.0;
+            const ff gm1 = {(float)gm1d, (float)(gm1d - (double)(float)gm1d)};
+            double f0[3], f1[3];
+            euler_flux_ff<1>(h0, gm1, f0);
+            euler_flux_ff<1>(h1, gm1, f1);
+            for (int v = 0; v < 3; ++v) B[v] = f1[v] - f0[v];
+        }
         for (int v = 0; v < 3; ++v) {
             double Wn, Sn;
             if (STAGE == 1) {
                 double W = g.S0[v * P + i];
-                Wn = W - ((double)xr(v) - (double)xl(v)) * idx;
-                Sn = ((double)xr(8 + v) - (double)xl(8 + v)) * idx;
+                const double dtd = *g.dt;
+                Wn = W - (((double)xr(v) - (double)xl(v)) + 0.5 * dtd * B[v]) * idx;
+                Sn = (((double)xr(8 + v) - (double)xl(8 + v)) + hd[v]) * idx;
                 if (!BULK32) g.S1[v * P + i] = Wn;  // the FP32-bulk stage 2 reads the float planes
-                g.ACC[v * P + i] = W - ((double)xr(4 + v) - (double)xl(4 + v)) * idx;
-                g.ACC[(3 + v) * P + i] = ((double)xr(12 + v) - (double)xl(12 + v)) * idx;
+                g.ACC[v * P + i] = W - (((double)xr(4 + v) - (double)xl(4 + v)) + dtd * B[v]) * idx;
+                g.ACC[(3 + v) * P + i] = (((double)xr(12 + v) - (double)xl(12 + v)) + hd[v]) * idx;
             } else {
                 Wn = g.ACC[v * P + i] - ((double)xr(v) - (double)xl(v)) * idx;
                 Sn = g.ACC[(3 + v) * P + i] + ((double)xr(4 + v) - (double)xl(4 + v)) * idx;
@@ -846,7 +1054,9 @@ __global__ void __launch_bounds__(256) k_update1(Work w)
             }
             if (BULK32) {
                 float* outf = STAGE == 1 ? g.F1 : g.F0;
-                outf[v * P + i] = (float)Wn;
+                const float hi = (float)Wn;
+                outf[v * P + i] = hi;
+                outf[(6 + v) * P + i] = (float)(Wn - (double)hi);  // low part
                 outf[(3 + v) * P + i] = (float)Sn;
             } else {
                 (STAGE == 1 ? g.S1 : g.S0)[(3 + v) * P + i] = Sn;
@@ -881,6 +1091,8 @@ __global__ void __launch_bounds__(256) k_convert(Work w, int to_float)
         long long P = g.plane;
         if (to_float) {
             for (int p = 0; p < NP; ++p) g.F0[p * P + c] = (float)g.S0[p * P + c];
+            // low parts of the cell averages, after the other planes
+            for (int v = 0; v < NV; ++v) g.F0[(NP + v) * P + c] = low_part<float>(g.S0[v * P + c]);
         } else {
             for (int p = NV; p < NP; ++p) g.S0[p * P + c] = (double)g.F0[p * P + c];
         }
