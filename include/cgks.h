@@ -240,6 +240,15 @@ int cgks_step_info(cgks_solver* s, int* kernels_per_step);
  * Advances the state like cgks_step. */
 int cgks_profile_step(cgks_solver* s, double dt, float* ms, int* ids, int* n);
 
+/* Diagnostics for the roofline of the stage kernels (no counterpart in the
+ * paper): the measured fused multiply-add throughput of the current GPU in
+ * precision CGKS_FP32_BULK (FP32) or CGKS_FP64, from a kernel of independent
+ * FMA chains on every SM (2 flops per FMA), timed with CUDA events at the
+ * clock the GPU runs at; *tflops receives TFLOP/s, ms (may be NULL) the best
+ * launch time.  Allocates a small output buffer; synchronous; changes no
+ * GPU setting.  CGKS_EINVAL for a NULL tflops or another precision. */
+int cgks_fma_peak(int precision, double* tflops, float* ms);
+
 void cgks_destroy(cgks_solver* s);
 const char* cgks_strerror(int code);
 

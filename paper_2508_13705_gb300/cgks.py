@@ -32,7 +32,7 @@ EXPORTS = ("cgks_default_params", "cgks_init_mesh", "cgks_set_state", "cgks_set_
            "cgks_batch_step", "cgks_batch_sync", "cgks_batch_get_state", "cgks_batch_destroy",
            "cgks_stencil_row", "cgks_profile_step", "cgks_step_1d_noalloc", "cgks_autotune",
            "cgks_batch_autotune", "cgks_set_time", "cgks_batch_set_state_device",
-           "cgks_batch_get_state_device")
+           "cgks_batch_get_state_device", "cgks_fma_peak")
 
 
 class Params(ctypes.Structure):
@@ -102,6 +102,7 @@ def lib():
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
         L.cgks_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
         L.cgks_batch_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+        L.cgks_fma_peak.argtypes = [ip, dp, ctypes.POINTER(ctypes.c_float)]
         L.cgks_step_1d_noalloc.argtypes = [ctypes.POINTER(Params), ip, ctypes.c_double, ctypes.c_double,
                                            vp, vp, vp, vp, ctypes.c_double, vp, vp]
         _lib = L
@@ -370,6 +371,14 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def fma_peak(precision):
+    """Measured FMA throughput of the current GPU (TFLOP/s) in FP32 or FP64."""
+    t = ctypes.c_double()
+    ms = ctypes.c_float()
+    _check(lib().cgks_fma_peak(precision, ctypes.byref(t), ctypes.byref(ms)), "cgks_fma_peak")
+    return t.value, ms.value
 
 
 def stencil_row(order, st, row):

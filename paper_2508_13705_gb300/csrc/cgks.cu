@@ -244,7 +244,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // per-mesh slab layout
 struct Layout {
-    size_t S, F, ACC, sigx, sigy, LA[2], FR[2], FO[2], SP[2], AT[2], DN[2], scal, total;
+    size_t S, F, ACC, sigx, sigy, LA[2], FR[2], FO[2], SP[2], AT[2], DN[2], TD[2], scal, total;
 };
 
 Layout layout(int dim, int M, size_t rs, int nx, int ny)
@@ -270,6 +270,8 @@ Layout layout(int dim, int M, size_t rs, int nx, int ny)
         L.SP[d] = o; o = align256(o + (on ? (size_t)nb * (na + 1) * M * 8 : 0));
         L.AT[d] = o; o = align256(o + (on && dim == 2 ? (size_t)(nb + 2) * (na + 6) * rs : 0));
         L.DN[d] = o; o = align256(o + (on && dim == 2 ? (size_t)(nb + 2) * (na + 6) * 4 * rs : 0));
+        // FP32 bulk: each cell's tangential differences of hi, for Step 3
+        L.TD[d] = o; o = align256(o + (on && dim == 2 && rs == 4 ? (size_t)(nb + 2) * (na + 6) * 8 * rs : 0));
     }
     L.scal = o; o = align256(o + 512);
     L.total = o;
@@ -367,6 +369,7 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
             g.SP[d] = (double*)(m0 + L[k].SP[d]);
             g.AT[d] = m0 + L[k].AT[d];
             g.DN[d] = m0 + L[k].DN[d];
+            g.TD[d] = m0 + L[k].TD[d];
         }
         char* sc = m0 + L[k].scal;
         g.dt = (double*)sc;
@@ -543,25 +546,30 @@ int grid_for(cgks_batch* b, const void* fn, int threads)
 
 // Time each stage kernel at every admissible block size on the current state
 // and keep the fastest.  Only kernels that write scratch data run (stage 1
-// lines / normal / flux / update and the stage-2 flux); the simulated time is
-// restored afterwards.  The step graphs are rebuilt on next use.
+// lines / normal / flux / update and the stage-2 flux); the simulated time,
+// the fallback count and the status word are restored afterwards.  The step
+// graphs are rebuilt on next use.
 int autotune(cgks_batch* b, int* out)
 {
     if (!b->state_set) return CGKS_EINVAL;
     // tuning order: each kernel runs after the producers of its inputs (the
-    // stage-2 flux before the stage-1 flux, so the update sees stage-1 data)
-    const void* fns[5] = {(const void*)b->k.lines, (const void*)b->k.normal, (const void*)b->k.flux2,
-                          (const void*)b->k.flux1, (const void*)b->k.upd1};
-    const int slots[5] = {0, 1, 3, 2, 4};
-    const int kinds[5] = {W_LINES, W_NORMAL, W_FLUX, W_FLUX, W_CELLS};
+    // stage-2 flux last: it reads the stage-1 state W* that the update writes)
+    const void* fns[5] = {(const void*)b->k.lines, (const void*)b->k.normal, (const void*)b->k.flux1,
+                          (const void*)b->k.upd1, (const void*)b->k.flux2};
+    const int slots[5] = {0, 1, 2, 4, 3};
+    const int kinds[5] = {W_LINES, W_NORMAL, W_FLUX, W_CELLS, W_FLUX};
     const int stages[5] = {1, 1, 0, 0, 0};
     const bool has_stage[5] = {true, true, false, false, false};
     std::vector<double> t_saved(b->n), tn_saved(b->n);
     std::vector<unsigned long long> nf_saved(b->n);
+    std::vector<unsigned> st_saved(b->n);
+    std::vector<long long> bad_saved(b->n);
     for (int k = 0; k < b->n; ++k) {
         CK(cudaMemcpy(&t_saved[k], b->host[k].t, 8, cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(&tn_saved[k], b->host[k].tn, 8, cudaMemcpyDeviceToHost));
         CK(cudaMemcpy(&nf_saved[k], b->host[k].nfall, 8, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&st_saved[k], b->host[k].status, 4, cudaMemcpyDeviceToHost));
+        CK(cudaMemcpy(&bad_saved[k], b->host[k].bad, 8, cudaMemcpyDeviceToHost));
     }
     // a CFL time step so that every kernel sees the data of a real step
     int r = launch(b, (const void*)b->k.cfl, W_CELLS, 6, 0, false);
@@ -625,6 +633,8 @@ int autotune(cgks_batch* b, int* out)
         CK(cudaMemcpy(b->host[k].t, &t_saved[k], 8, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(b->host[k].tn, &tn_saved[k], 8, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(b->host[k].nfall, &nf_saved[k], 8, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b->host[k].status, &st_saved[k], 4, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(b->host[k].bad, &bad_saved[k], 8, cudaMemcpyHostToDevice));
     }
     for (int g = 0; g < 2; ++g)
         if (b->gexec[g]) { cudaGraphExecDestroy(b->gexec[g]); b->gexec[g] = nullptr; }

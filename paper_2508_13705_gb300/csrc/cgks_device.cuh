@@ -88,6 +88,8 @@ struct Mesh {
     void *LA[2], *FR[2], *FO[2];    // scratch per direction (R typed)
     void* AT[2];                    // tangential r5 DFF per cell (R typed)
     void* DN[2];                    // normal-direction DFF of each cell, packed [4] (R typed)
+    void* TD[2];                    // FP32 bulk: hi(a, b-1) - hi(a, b), hi(a, b+1) - hi(a, b)
+                                    // of each cell, local frame, [8] floats
     double* SP[2];                  // sigma per face Gauss point
     double* dt;                     // device scalar (this mesh's step)
     float* dtf;                     // the same in FP32

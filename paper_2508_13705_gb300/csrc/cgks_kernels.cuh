@@ -22,14 +22,17 @@
 //   SP  [nb][na+1][M]                 sigma per face Gauss point (Eq. 3.2)
 //   AT  [nb+2][na+6]                  tangential r5 DFF of each cell (Step 3)
 //   DN  [nb+2][na+6][4]               normal-direction DFF of each cell (Step 2), packed
+//   TD  [nb+2][na+6][8]               FP32 bulk: the cell's tangential differences of hi,
+//                                     hi(a, b-1) - hi(a, b) and hi(a, b+1) - hi(a, b), for
+//                                     the bases of the Step 3 segments
 //
 // FP32-bulk form: a cell average W (FP64) is held in the float planes as
 // hi = float(W) and lo = float(W - hi), and every reconstructed quantity that
 // is a value (line averages, face states, the equilibrium state, the
 // interface states) is carried as an increment over the hi of one cell: the
-// line average of cell i as lo_i + (its reconstruction's increment), a face
-// state of cell i as an increment over hi_i, the face's equilibrium state and
-// interface states as increments over hi of the face's right cell.  Stencil
+// line average of cell i as lo_i + (its reconstruction's increment), both
+// states of a face, its equilibrium state and its interface states as
+// increments over hi of the face's right cell.  Stencil
 // data enter as differences (hi_k - hi_i) + (lo_k - lo_i), exact in float
 // for neighbouring values, so the FP32 arithmetic only ever rounds small
 // increments; the O(1) Euler flux of the base hi is formed in float-float in
@@ -190,6 +193,14 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
         R* LA = (R*)g.LA[dir] + cidx * 4;
         // tangential r5 DFF of this cell, reused by Step 3 in k_flux
         ((R*)g.AT[dir])[cidx] = (R)dff.a[3];
+        if (BULK32) {
+            // the tangential differences of hi, for the bases of Step 3's segments
+            R tdm[4], tdp[4];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) { tdm[v] = sw[v][1] - sw[v][2]; tdp[v] = sw[v][3] - sw[v][2]; }
+            st4((R*)g.TD[dir] + cidx * 8, tdm);
+            st4((R*)g.TD[dir] + cidx * 8 + 4, tdp);
+        }
         // normal-direction DFF of this cell, reused by every Gauss line in k_normal
         if (a >= -1 && a <= na) {
             double n6[6];
@@ -348,7 +359,10 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
                     }
                     R out[6];
                     recon_st<R, 6, (M >= 2 ? M - 2 : 0), ST, 0>(dff, dp, out, ghi, glo, eps);
-                    sideL[0][v] = qi + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
+                    // FP32 bulk: the left state of face a+1 over the hi of that face's
+                    // right cell a+1, like the right state: a face's two states share a base
+                    const R shift = BULK32 ? sh[BULK32 ? v : 0][2] - sh[BULK32 ? v : 0][3] : (R)0;
+                    sideL[0][v] = (qi + shift) + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
                     sideR[0][v] = qi + out[3]; sideR[1][v] = out[4] * ih; sideR[2][v] = out[5] * ih * ih;
                 }
             });
@@ -366,10 +380,12 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
                     if (BULK32) dp[q] += cell<1, 1, R, WALLS>(g, S, 5, v, 0, a + q - 2, 0, tb) - ql;
                     dp[5 + q] = hn * cell<1, 1, R, WALLS>(g, S, 1, v, 0, a + q - 2, 0, tb);
                 }
+                // the left state of face a+1 over hi of cell a+1 (a face's states share a base)
+                const R shift = BULK32 ? qi - cell<1, 1, R, WALLS>(g, S, 0, v, 0, a + 1, 0, tb) : (R)0;
                 if (BULK32) qi = ql;
                 R out[6];
                 recon<R, 6>(dff, g.oi, 0, dp, out, ghi, glo, eps);
-                sideL[0][v] = qi + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
+                sideL[0][v] = (qi + shift) + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
                 sideR[0][v] = qi + out[3]; sideR[1][v] = out[4] * ih; sideR[2][v] = out[5] * ih * ih;
             }
         }
@@ -458,37 +474,32 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         const long long npt = fr_npt(na, nb, M);
         const long long p00 = fr_row(dir, na, nb, b, f) * M;
         const long long rs = (dir == 0 ? (long long)(na + 1) : 1LL) * M;  // FR row stride of the segments
-        // FP32 bulk: the state planes of this stage, whose high parts hi are the
-        // bases of the face states (local frame); hi of cell (a, bb)
+        // FP32 bulk: the state planes of this stage, whose high part hi of the
+        // face's right cell f is the base of both face states (local frame)
         const R* SF = state_planes<R>(g, STAGE == 1 ? 0 : 1);
         const double tb = stage_time(g, STAGE);
-        auto hi_of = [&](int a, int bb, R out[4]) {
-            if (a >= 0 && a < na && bb >= 0 && bb < nb) {
-                long long ci = dir == 0 ? (long long)bb * g.nx + a : (long long)a * g.nx + bb;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) out[v] = SF[vglob(dir, v) * g.plane + ci];
-            } else {
-#pragma unroll
-                for (int v = 0; v < NV; ++v) out[v] = lcell<D, M, R, true>(g, SF, dir, 0, v, 0, a, bb, tb);
-            }
-            if (NV < 4) out[3] = (R)0;
-        };
-        // W_l - W_r from differences of hi and of the increments, and whether it
-        // is small enough for the kinetic weighting to be taken to first order
-        // in it (below); hb1: hi of the right cell f, the base of the face
-        R hb1[4], dW[4] = {0, 0, 0, 0}, Dl[4] = {0, 0, 0, 0};
+        // W_l - W_r as the difference of the two increments, and whether it is
+        // small enough for the kinetic weighting to be taken to first order in
+        // it (below); hb1: hi of the right cell f
+        R hb1[4] = {0, 0, 0, 0}, dW[4] = {0, 0, 0, 0}, Dl[4] = {0, 0, 0, 0};
         bool lin = false;
         if (BULK32) {
-            R hb0[4], e0[4], e1[4];
-            hi_of(f - 1, b, hb0);
-            hi_of(f, b, hb1);
+            if (f < na && (D == 1 || b < nb)) {
+                long long ci = dir == 0 ? (long long)b * g.nx + f : (long long)f * g.nx + b;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) hb1[v] = SF[vglob(dir, v) * g.plane + ci];
+            } else {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) hb1[v] = lcell<D, M, R, true>(g, SF, dir, 0, v, 0, f, b, tb);
+            }
+            R e0[4], e1[4];
             ld4(FR + (p00 + rs + l) * 8, e0);
             ld4(FR + npt * 12 + (p00 + rs + l) * 8, e1);
             R sc = fabs(hb1[0]) + fabs(hb1[NV - 1]);
             lin = true;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                dW[v] = (hb0[v] - hb1[v]) + (e0[v] - e1[v]);
+                dW[v] = e0[v] - e1[v];
                 lin &= fabs(dW[v]) <= (R)2.5e-4 * sc;
             }
         }
@@ -504,11 +515,9 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         bool bad = false, ok = true;
 #pragma unroll 1
         for (int side = 0; side < 2; ++side) {
-            // Step 2 data: W, W_n, W_nn (FP32 bulk: W as an increment over hb)
+            // Step 2 data: W, W_n, W_nn (FP32 bulk: W as an increment over hb1)
             R d[6][4];
             const int a = side == 0 ? f - 1 : f;  // the reconstructing cell
-            R hb[4] = {0, 0, 0, 0};
-            if (BULK32) hi_of(a, b, hb);
             const R* Fs = FR + side * npt * 12 + p00 * 8;  // (W, W_n) of segment b - 1
             ld4(Fs + (rs + l) * 8, d[0]);
             ld4(Fs + (rs + l) * 8 + 4, d[1]);
@@ -538,17 +547,17 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
                         }
                     }
                 if (BULK32) {
-                    // the segment points' values are increments over the hi of
-                    // their own cells: add the bases' part, with the weights of
-                    // a constant summing to zero
-                    R hm[4], hp[4];
-                    hi_of(a, b - 1, hm);
-                    hi_of(a, b + 1, hp);
+                    // the segment points' values are increments over hi of the
+                    // right cells (f, b-1), (f, b), (f, b+1): add the bases' part
+                    // from their differences (the weights of a constant sum to zero)
+                    R dm[4], dpl[4];
+                    const R* td = (const R*)g.TD[dir] + cell_idx(dir, na, nb, f, b) * 8;
+                    ld4(td, dm);
+                    ld4(td + 4, dpl);
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
-                        R dm = hm[v] - hb[v], dpl = hp[v] - hb[v];
-                        wt[v] += s_c1[l][0] * dm + s_c1[l][2] * dpl;
-                        wtt[v] += s_c2[l][0] * dm + s_c2[l][2] * dpl;
+                        wt[v] += s_c1[l][0] * dm[v] + s_c1[l][2] * dpl[v];
+                        wtt[v] += s_c2[l][0] * dm[v] + s_c2[l][2] * dpl[v];
                     }
                 }
 #pragma unroll
@@ -561,22 +570,27 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
             // the side's state
             R ws[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) ws[v] = BULK32 ? hb[v] + d[0][v] : d[0][v];
+            for (int v = 0; v < 4; ++v) ws[v] = BULK32 ? hb1[v] + d[0][v] : d[0][v];
             if (PF) {
                 // fallback: a side whose point state has rho <= 0 or p <= 0 takes
                 // the average of the cell it was reconstructed from, first order;
                 // the test is made in FP64 (FP32 bulk: on hi + increment)
                 double W4[4];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) W4[v] = BULK32 ? (double)hb[v] + (double)d[0][v] : (double)d[0][v];
+                for (int v = 0; v < 4; ++v) W4[v] = BULK32 ? (double)hb1[v] + (double)d[0][v] : (double)d[0][v];
                 double rho = W4[0];
                 double m2 = W4[1] * W4[1] + (D == 2 ? W4[2] * W4[2] : 0.0);
                 double p = (g.gamma - 1.0) * (W4[NV - 1] - 0.5 * m2 / rho);
                 if (!(rho > 0.0) || !(p > 0.0)) {
 #pragma unroll
                     for (int v = 0; v < NV; ++v) {
-                        d[0][v] = lcell<D, M, R, true>(g, SF, dir, BULK32 ? 5 : 0, v, 0, a, b, tb);
-                        ws[v] = BULK32 ? hb[v] + d[0][v] : d[0][v];
+                        // FP32 bulk: the average over hb1, (hi_a - hb1) + lo_a
+                        if (BULK32)
+                            d[0][v] = (side == 0 ? lcell<D, M, R, true>(g, SF, dir, 0, v, 0, a, b, tb) - hb1[v] : (R)0)
+                                    + lcell<D, M, R, true>(g, SF, dir, 5, v, 0, a, b, tb);
+                        else
+                            d[0][v] = lcell<D, M, R, true>(g, SF, dir, 0, v, 0, a, b, tb);
+                        ws[v] = BULK32 ? hb1[v] + d[0][v] : d[0][v];
 #pragma unroll
                         for (int q = 1; q < 6; ++q) d[q][v] = (R)0;
                     }

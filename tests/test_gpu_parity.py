@@ -343,12 +343,14 @@ def test_fp32_bulk_quadrants_per_step():
 
 # ---------------------------------------------------------------- autotuner
 
-def test_autotune_keeps_results_bitwise_and_state():
-    """The autotuner changes only launch shapes: the state is not advanced and
-    the following steps are bitwise equal to an untuned solver's."""
+@pytest.mark.parametrize("precision", [cgks.FP64, cgks.FP32_BULK])
+def test_autotune_keeps_results_bitwise_and_state(precision):
+    """The autotuner changes only launch shapes: the state is not advanced, the
+    device status stays clear, and the following steps are bitwise equal to
+    an untuned solver's."""
     n = 40
     st = inputs.quadrants_2d(n, 9, seed=2)
-    kw = dict(tau_mode=cgks.TAU_HGKS, bc=(1, 1, 1, 1))
+    kw = dict(tau_mode=cgks.TAU_HGKS, bc=(1, 1, 1, 1), precision=precision)
     outs = []
     for tune in (False, True):
         s = cgks.Solver(2, 9, n, n, **kw)
@@ -363,6 +365,7 @@ def test_autotune_keeps_results_bitwise_and_state():
                 assert np.array_equal(before[f], after[f]), f
         s.advance(4, 0.0)
         t, rc, _ = s.sync()
+        assert rc == 0
         outs.append((t, s.get_state()))
     assert outs[0][0] == outs[1][0]
     for f in FIELDS_2D:
