@@ -182,7 +182,7 @@ def nproc():
         return os.cpu_count() or 1
 
 
-KERNEL_NAMES = {0: "lines", 1: "normal", 2: "flux", 3: "update", 4: "dt"}
+KERNEL_NAMES = {0: "recon_x", 1: "recon_y", 2: "flux", 3: "update", 4: "dt"}
 
 
 def kernel_ms(prof):

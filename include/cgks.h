@@ -216,16 +216,21 @@ int cgks_get_state_device(cgks_solver* s, double* W, double* Wx, double* Wy, dou
 /* Diagnostics (synchronous). */
 int cgks_get_stats(cgks_solver* s, cgks_stats* st);
 
-/* Autotuner: times every stage kernel on the solver's current state at each
- * admissible block size (64..512 threads, persistent grid = SM count x
- * resident blocks) and keeps the fastest; the step graph is rebuilt on the
- * next step.  The state is not advanced (only scratch is written; the
- * simulated time is restored) and results do not depend on the choice: every
- * work item is computed by one thread.  The flux kernels are also timed in
- * a register-capped variant (more resident warps, some spilling).
- * threads_out (may be NULL) receives the block sizes of lines, normal, flux
- * (stage 1, 2), update (stage 1, 2); a negative flux entry marks the capped
- * variant.  Requires a state (CGKS_EINVAL otherwise). */
+/* Autotuner: times every stage kernel on the solver's current state and keeps
+ * the fastest launch shape; the step graph is rebuilt on the next step.  The
+ * 2-D Steps 1-2 (one fused kernel per direction over tiles held in shared
+ * memory) are timed over tile shapes TA x TB (cells along the face normal x
+ * across it: 28x8, 60x4, 12x16, 28x4, 12x8, 124x2) at 128 and 256 threads;
+ * the other kernels over block sizes 64..512 (persistent grid = SM count x
+ * resident blocks), the flux kernels also in a register-capped variant (more
+ * resident warps, some spilling).  The state is not advanced (only scratch is
+ * written; the simulated time, the status word and the fallback count are
+ * restored) and results do not depend on the choice: every work item is
+ * computed by one thread.  threads_out (may be NULL) receives 10 ints: the
+ * block sizes of Steps 1-2 along x and y (1-D: 0 and Step 2), flux (stage 1,
+ * 2), update (stage 1, 2), then the tile shapes (TA, TB) along x and y (0 in
+ * 1-D); a negative flux entry marks the capped variant.  Requires a state
+ * (CGKS_EINVAL otherwise). */
 int cgks_autotune(cgks_solver* s, int* threads_out);
 int cgks_batch_autotune(cgks_batch* b, int* threads_out);
 
@@ -235,8 +240,8 @@ int cgks_step_info(cgks_solver* s, int* kernels_per_step);
 /* Diagnostics: run one fixed-dt step (dt > 0) kernel by kernel outside the
  * graph, with CUDA events on the solver's stream between launches.  ms[k]
  * receives the device time of launch k and ids[k] its kernel:
- * 0 lines, 1 normal, 2 flux, 3 update, 4 dt (stage s launches carry
- * 10*s + id).  *n is the capacity on entry and the count on exit (<= 16).
+ * 0 Steps 1-2 along x (2-D), 1 Steps 1-2 along y (2-D) or Step 2 (1-D),
+ * 2 flux, 3 update, 4 dt (stage s launches carry 10*s + id).  *n is the capacity on entry and the count on exit (<= 16).
  * Advances the state like cgks_step. */
 int cgks_profile_step(cgks_solver* s, double dt, float* ms, int* ids, int* n);
 

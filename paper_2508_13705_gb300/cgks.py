@@ -135,6 +135,16 @@ def _dev(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+TUNED_KEYS = ("recon_x", "recon_y", "flux1", "flux2", "update1", "update2", "tile_x", "tile_y")
+
+
+def _tuned(fn, h):
+    t = (ctypes.c_int * 10)()
+    _check(fn(h, t), "autotune")
+    v = list(t)
+    return dict(zip(TUNED_KEYS, v[:6] + [(v[6], v[7]), (v[8], v[9])]))
+
+
 def make_params(dim, order, precision=FP64, tau_mode=TAU_ZERO, bc=(BC_PERIODIC,) * 4, **kw):
     p = Params()
     _check(lib().cgks_default_params(ctypes.byref(p), dim, order), "cgks_default_params")
@@ -272,10 +282,8 @@ class Solver:
         _check(lib().cgks_set_time(self.h, float(t)), "cgks_set_time")
 
     def autotune(self):
-        """Pick each stage kernel's block size by timing it on the current state."""
-        t = (ctypes.c_int * 6)()
-        _check(lib().cgks_autotune(self.h, t), "cgks_autotune")
-        return dict(zip(("lines", "normal", "flux1", "flux2", "update1", "update2"), list(t)))
+        """Pick each stage kernel's launch shape by timing it on the current state."""
+        return _tuned(lib().cgks_autotune, self.h)
 
     def kernels_per_step(self):
         n = ctypes.c_int()
@@ -349,9 +357,7 @@ class Batch:
         _check(lib().cgks_batch_sync(self.h), "cgks_batch_sync")
 
     def autotune(self):
-        t = (ctypes.c_int * 6)()
-        _check(lib().cgks_batch_autotune(self.h, t), "cgks_batch_autotune")
-        return dict(zip(("lines", "normal", "flux1", "flux2", "update1", "update2"), list(t)))
+        return _tuned(lib().cgks_batch_autotune, self.h)
 
     def get_state(self, k):
         c = (4, self.ny[k], self.nx[k])

@@ -83,11 +83,19 @@ Kfns pick_kfns(int dim, int order, int prec, int tau_mode, const int bc[4], int 
     // stencil kernels with the wall ghost rules only where a side is a wall
     bool walls = false;
     for (int s = 0; s < (dim == 2 ? 4 : 2); ++s) walls = walls || bc[s] >= CGKS_BC_REFLECTIVE;
-    if (walls) { k.lines = k.linesw; k.normal = k.normalw; }
+    if (walls) { k.recon[0] = k.reconw[0]; k.recon[1] = k.reconw[1]; k.normal = k.normalw; }
     return k;
 }
 
-enum { W_LINES = 0, W_NORMAL, W_FLUX, W_CELLS, W_SIGINIT, W_COUNT };
+// Work lists: tiles of the 2-D Steps 1-2 per direction (their counts follow
+// the tile shape of each direction), 1-D cells of Step 2, face points, cells,
+// faces.
+enum { W_TILE0 = 0, W_TILE1, W_NORMAL, W_FLUX, W_CELLS, W_SIGINIT, W_COUNT };
+
+// Tile shapes (cells along the normal x across it) the autotuner tries for
+// the 2-D Steps 1-2; the first is the default.
+const int kTileShapes[][2] = {{28, 8}, {60, 4}, {12, 16}, {28, 4}, {12, 8}, {124, 2}};
+const int kNumTileShapes = 6;
 
 } // namespace
 
@@ -106,6 +114,7 @@ struct cgks_batch {
     Kfns k;
     int grid[16];
     int threads[16];  // threads per block of each kernel slot (autotuned)
+    int tile[2][2];   // 2-D Steps 1-2: tile shape (TA, TB) per direction (autotuned)
     int nsm = 0;
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};  // [0] fixed dt, [1] CFL dt
     int kernels_per_step = 0;
@@ -136,11 +145,20 @@ Work work_of(const cgks_batch* b, int kind)
     return w;
 }
 
+// Tiles of TA x TB cells covering a in [-1, na], b in [-1, nb] of direction dir.
+long long tiles(int dir, int nx, int ny, int TA, int TB)
+{
+    long long na = dir == 0 ? nx : ny, nb = dir == 0 ? ny : nx;
+    return ((na + 2 + TA - 1) / TA) * ((nb + 2 + TB - 1) / TB);
+}
+
 long long items(int kind, int dim, int M, int nx, int ny)
 {
+    (void)M;
     switch (kind) {
-    case W_LINES: return dim == 2 ? (long long)(nx + 6) * (ny + 2) + (long long)(ny + 6) * (nx + 2) : 0;
-    case W_NORMAL: return dim == 2 ? 2LL * (nx + 2) * (ny + 2) * M : nx + 2;
+    case W_TILE0: return dim == 2 ? tiles(0, nx, ny, kTileShapes[0][0], kTileShapes[0][1]) : 0;
+    case W_TILE1: return dim == 2 ? tiles(1, nx, ny, kTileShapes[0][0], kTileShapes[0][1]) : 0;
+    case W_NORMAL: return dim == 2 ? 0 : nx + 2;
     case W_FLUX: return dim == 2 ? ((long long)(nx + 1) * ny + (long long)(ny + 1) * nx) * M : nx + 1;
     case W_CELLS: return (long long)nx * ny;
     default: return dim == 2 ? (long long)(nx + 1) * ny + (long long)(ny + 1) * nx : nx + 1;
@@ -161,11 +179,57 @@ int launch(cgks_batch* b, const void* fn, int kind, int gi, int stage, bool has_
     return CGKS_OK;
 }
 
+// Dynamic shared memory of the 2-D Steps 1-2 for a tile shape.
+size_t recon_smem(const cgks_batch* b, int TA, int TB)
+{
+    return (size_t)(TA + 4) * TB * (4 * b->M + 8) * b->rsize;
+}
+
+// Set the tile shape of direction dir: the per-mesh tile counts of the work
+// list (host and device), the kernel's shared-memory limit and its persistent
+// grid at `threads` threads per block (slot dir).
+int set_tile(cgks_batch* b, int dir, int TA, int TB, int threads)
+{
+    const void* fn = (const void*)b->k.recon[dir];
+    size_t smem = recon_smem(b, TA, TB);
+    CK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, smem) != cudaSuccess || occ < 1)
+        return CGKS_ENOTSUP;
+    b->tile[dir][0] = TA;
+    b->tile[dir][1] = TB;
+    b->threads[dir] = threads;
+    b->grid[dir] = occ * b->nsm;
+    const int kind = dir == 0 ? W_TILE0 : W_TILE1;
+    long long* o = b->off.data() + (size_t)kind * (b->n + 1);
+    o[0] = 0;
+    for (int k = 0; k < b->n; ++k) o[k + 1] = o[k] + tiles(dir, b->host[k].nx, b->host[k].ny, TA, TB);
+    CK(cudaMemcpy(b->doff + (size_t)kind * (b->n + 1), o, (b->n + 1) * sizeof(long long), cudaMemcpyHostToDevice));
+    return CGKS_OK;
+}
+
+// One launch of the 2-D Steps 1-2 of direction dir (tiles as work items).
+int launch_recon(cgks_batch* b, int dir, int stage)
+{
+    Work w = work_of(b, dir == 0 ? W_TILE0 : W_TILE1);
+    if (w.total == 0) return CGKS_OK;
+    int TA = b->tile[dir][0], TB = b->tile[dir][1];
+    int grid = (int)std::max<long long>(1, std::min<long long>(w.total, (long long)b->grid[dir]));
+    void* args[] = {&w, &stage, &TA, &TB};
+    CK(cudaLaunchKernel((const void*)b->k.recon[dir], dim3(grid), dim3(b->threads[dir]), args,
+                        recon_smem(b, TA, TB), b->stream));
+    return CGKS_OK;
+}
+
 int enqueue_stage(cgks_batch* b, int stage)
 {
     int r;
-    if (b->dim == 2 && (r = launch(b, (const void*)b->k.lines, W_LINES, 0, stage, true))) return r;
-    if ((r = launch(b, (const void*)b->k.normal, W_NORMAL, 1, stage, true))) return r;
+    if (b->dim == 2) {
+        if ((r = launch_recon(b, 0, stage))) return r;
+        if ((r = launch_recon(b, 1, stage))) return r;
+    } else if ((r = launch(b, (const void*)b->k.normal, W_NORMAL, 1, stage, true))) {
+        return r;
+    }
     if ((r = launch(b, (const void*)(stage == 1 ? b->k.flux1 : b->k.flux2), W_FLUX, stage == 1 ? 2 : 3, 0, false))) return r;
     if ((r = launch(b, (const void*)(stage == 1 ? b->k.upd1 : b->k.upd2), W_CELLS, stage == 1 ? 4 : 5, 0, false))) return r;
     return CGKS_OK;
@@ -244,7 +308,7 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // per-mesh slab layout
 struct Layout {
-    size_t S, F, ACC, sigx, sigy, LA[2], FR[2], FO[2], SP[2], AT[2], DN[2], TD[2], scal, total;
+    size_t S, F, ACC, sigx, sigy, FR[2], FO[2], SP[2], AT[2], TD[2], scal, total;
 };
 
 Layout layout(int dim, int M, size_t rs, int nx, int ny)
@@ -264,12 +328,10 @@ Layout layout(int dim, int M, size_t rs, int nx, int ny)
     for (int d = 0; d < 2; ++d) {
         int na = d == 0 ? nx : ny, nb = d == 0 ? ny : nx;
         bool on = dim == 2 || d == 0;
-        L.LA[d] = o; o = align256(o + (on && dim == 2 ? (size_t)(nb + 2) * (na + 6) * M * 4 * rs : 0));
         L.FR[d] = o; o = align256(o + (on ? (size_t)(nb + 2) * (na + 1) * M * 24 * rs : 0));
         L.FO[d] = o; o = align256(o + (on ? (size_t)nb * (na + 1) * M * 16 * rs : 0));
         L.SP[d] = o; o = align256(o + (on ? (size_t)nb * (na + 1) * M * 8 : 0));
         L.AT[d] = o; o = align256(o + (on && dim == 2 ? (size_t)(nb + 2) * (na + 6) * rs : 0));
-        L.DN[d] = o; o = align256(o + (on && dim == 2 ? (size_t)(nb + 2) * (na + 6) * 4 * rs : 0));
         // FP32 bulk: each cell's tangential differences of hi, for Step 3
         L.TD[d] = o; o = align256(o + (on && dim == 2 && rs == 4 ? (size_t)(nb + 2) * (na + 6) * 8 * rs : 0));
     }
@@ -363,12 +425,10 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         g.sig_y = p->dim == 2 ? (double*)(m0 + L[k].sigy) : nullptr;
         g.sig_yn = p->dim == 2 ? g.sig_y + (size_t)(ny[k] + 1) * nx[k] : nullptr;
         for (int d = 0; d < 2; ++d) {
-            g.LA[d] = m0 + L[k].LA[d];
             g.FR[d] = m0 + L[k].FR[d];
             g.FO[d] = m0 + L[k].FO[d];
             g.SP[d] = (double*)(m0 + L[k].SP[d]);
             g.AT[d] = m0 + L[k].AT[d];
-            g.DN[d] = m0 + L[k].DN[d];
             g.TD[d] = m0 + L[k].TD[d];
         }
         char* sc = m0 + L[k].scal;
@@ -413,7 +473,7 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         int dev;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, dev);
-        const void* fns[7] = {(const void*)b->k.lines, (const void*)b->k.normal, (const void*)b->k.flux1,
+        const void* fns[7] = {nullptr, (const void*)b->k.normal, (const void*)b->k.flux1,
                               (const void*)b->k.flux2, (const void*)b->k.upd1, (const void*)b->k.upd2,
                               (const void*)b->k.cfl};
         for (int q = 0; q < 7; ++q) {
@@ -425,6 +485,10 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
             }
             b->grid[q] = std::max(1, occ) * b->nsm;
         }
+        // 2-D Steps 1-2: the default tile shape in both directions
+        if (p->dim == 2)
+            for (int d = 0; d < 2; ++d)
+                if ((rr = set_tile(b, d, kTileShapes[0][0], kTileShapes[0][1], 256))) break;
     } while (0);
     if (rr) { cgks_batch_destroy(b); return rr; }
     *out = b;
@@ -553,13 +617,14 @@ int autotune(cgks_batch* b, int* out)
 {
     if (!b->state_set) return CGKS_EINVAL;
     // tuning order: each kernel runs after the producers of its inputs (the
-    // stage-2 flux last: it reads the stage-1 state W* that the update writes)
-    const void* fns[5] = {(const void*)b->k.lines, (const void*)b->k.normal, (const void*)b->k.flux1,
+    // stage-2 flux last: it reads the stage-1 state W* that the update writes);
+    // the 2-D Steps 1-2 are tuned first, over tile shapes and block sizes
+    const void* fns[4] = {b->dim == 1 ? (const void*)b->k.normal : nullptr, (const void*)b->k.flux1,
                           (const void*)b->k.upd1, (const void*)b->k.flux2};
-    const int slots[5] = {0, 1, 2, 4, 3};
-    const int kinds[5] = {W_LINES, W_NORMAL, W_FLUX, W_CELLS, W_FLUX};
-    const int stages[5] = {1, 1, 0, 0, 0};
-    const bool has_stage[5] = {true, true, false, false, false};
+    const int slots[4] = {1, 2, 4, 3};
+    const int kinds[4] = {W_NORMAL, W_FLUX, W_CELLS, W_FLUX};
+    const int stages[4] = {1, 0, 0, 0};
+    const bool has_stage[4] = {true, false, false, false};
     std::vector<double> t_saved(b->n), tn_saved(b->n);
     std::vector<unsigned long long> nf_saved(b->n);
     std::vector<unsigned> st_saved(b->n);
@@ -585,7 +650,29 @@ int autotune(cgks_batch* b, int* out)
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int qq = 0; qq < 5; ++qq) {
+    for (int dir = 0; dir < (b->dim == 2 ? 2 : 0); ++dir) {
+        float best = 1e30f;
+        int bt = b->tile[dir][0], bb = b->tile[dir][1], bth = b->threads[dir];
+        const int thr[2] = {128, 256};
+        for (int sh = 0; sh < kNumTileShapes; ++sh)
+            for (int c = 0; c < 2; ++c) {
+                int TA = kTileShapes[sh][0], TB = kTileShapes[sh][1];
+                if (set_tile(b, dir, TA, TB, thr[c]) != CGKS_OK) continue;  // no room on an SM
+                float acc = 0.f;
+                for (int rep = 0; rep < 4; ++rep) {
+                    CK(cudaEventRecord(e0, b->stream));
+                    if ((r = launch_recon(b, dir, 1))) return r;
+                    CK(cudaEventRecord(e1, b->stream));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    if (rep > 0) acc += ms;  // the first launch warms caches
+                }
+                if (acc < best) { best = acc; bt = TA; bb = TB; bth = thr[c]; }
+            }
+        if ((r = set_tile(b, dir, bt, bb, bth))) return r;
+    }
+    for (int qq = 0; qq < 4; ++qq) {
         if (!fns[qq]) continue;
         int q = slots[qq];
         // the flux kernels come in two register variants; the others in one
@@ -640,9 +727,12 @@ int autotune(cgks_batch* b, int* out)
         if (b->gexec[g]) { cudaGraphExecDestroy(b->gexec[g]); b->gexec[g] = nullptr; }
     if (out) {
         for (int q = 0; q < 6; ++q) out[q] = b->threads[q];
+        if (b->dim == 1) out[0] = 0;
         // register-capped flux variants are reported as a negative block size
         if (b->k.flux1v[1] != b->k.flux1v[0] && b->k.flux1 == b->k.flux1v[1]) out[2] = -out[2];
         if (b->k.flux2v[1] != b->k.flux2v[0] && b->k.flux2 == b->k.flux2v[1]) out[3] = -out[3];
+        for (int d = 0; d < 2; ++d)
+            for (int e = 0; e < 2; ++e) out[6 + 2 * d + e] = b->dim == 2 ? b->tile[d][e] : 0;
     }
     return CGKS_OK;
 }
@@ -896,9 +986,11 @@ int cgks_profile_step(cgks_solver* s, double dt, float* ms, int* ids, int* n)
     }
     for (int stage = 1; stage <= 2; ++stage) {
         if (b->dim == 2) {
-            if ((r = launch(b, (const void*)b->k.lines, W_LINES, 0, stage, true)) || (r = rec(10 * stage + 0))) goto done;
+            if ((r = launch_recon(b, 0, stage)) || (r = rec(10 * stage + 0))) goto done;
+            if ((r = launch_recon(b, 1, stage)) || (r = rec(10 * stage + 1))) goto done;
+        } else {
+            if ((r = launch(b, (const void*)b->k.normal, W_NORMAL, 1, stage, true)) || (r = rec(10 * stage + 1))) goto done;
         }
-        if ((r = launch(b, (const void*)b->k.normal, W_NORMAL, 1, stage, true)) || (r = rec(10 * stage + 1))) goto done;
         if ((r = launch(b, (const void*)(stage == 1 ? b->k.flux1 : b->k.flux2), W_FLUX, stage == 1 ? 2 : 3, 0, false)) ||
             (r = rec(10 * stage + 2))) goto done;
         if ((r = launch(b, (const void*)(stage == 1 ? b->k.upd1 : b->k.upd2), W_CELLS, stage == 1 ? 4 : 5, 0, false)) ||

@@ -85,9 +85,8 @@ struct Mesh {
     double *sig_x, *sig_y;          // sigma of the previous step [ny][nx+1], [ny+1][nx]
     double *sig_xn, *sig_yn;        // sigma being built this step
     const double* ghost;            // 1-D fixed BC ghost cells
-    void *LA[2], *FR[2], *FO[2];    // scratch per direction (R typed)
+    void *FR[2], *FO[2];            // scratch per direction (R typed)
     void* AT[2];                    // tangential r5 DFF per cell (R typed)
-    void* DN[2];                    // normal-direction DFF of each cell, packed [4] (R typed)
     void* TD[2];                    // FP32 bulk: hi(a, b-1) - hi(a, b), hi(a, b+1) - hi(a, b)
                                     // of each cell, local frame, [8] floats
     double* SP[2];                  // sigma per face Gauss point

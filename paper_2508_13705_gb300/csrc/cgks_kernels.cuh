@@ -9,9 +9,6 @@
 // Scratch layouts per mesh and direction (na, nb: cells along / across the
 // normal; M Gauss points per face).  Direction 0 as written; direction 1 with
 // the two spatial indices swapped, so the global x index is always fastest:
-//   LA  [M][nb+2][na+6][4]            line averages, b in [-1, nb], a in [-3, na+2]
-//                                     (FP32-bulk form: the line average minus the
-//                                     high part hi of the cell average, see below)
 //   FR  [2]{[nb+2][na+1][M][8], [nb+2][na+1][M][4]}
 //                                     face states: side 0 = left (from cell f-1),
 //                                     side 1 = right (from cell f); per side one
@@ -21,7 +18,6 @@
 //                                     one plane per output quantity and line
 //   SP  [nb][na+1][M]                 sigma per face Gauss point (Eq. 3.2)
 //   AT  [nb+2][na+6]                  tangential r5 DFF of each cell (Step 3)
-//   DN  [nb+2][na+6][4]               normal-direction DFF of each cell (Step 2), packed
 //   TD  [nb+2][na+6][8]               FP32 bulk: the cell's tangential differences of hi,
 //                                     hi(a, b-1) - hi(a, b) and hi(a, b+1) - hi(a, b), for
 //                                     the bases of the Step 3 segments
@@ -83,7 +79,7 @@ __device__ __forceinline__ double lsigT(const Mesh& g, const double* sx, const d
 // direction 1 the tangential index b (= i): in both directions the global x
 // index runs fastest, in memory and across threads, so every kernel walks the
 // SoA state planes with unit stride.
-//   cell_idx: a in [-3, na+2], b in [-1, nb]   (LA, AT, DN)
+//   cell_idx: a in [-3, na+2], b in [-1, nb]   (AT, TD)
 //   fr_row:   bb = b + 1 in [0, nb+1], f in [0, na]   (FR)
 //   pt_idx:   b in [0, nb), f in [0, na]       (FO, SP)
 __device__ __forceinline__ long long cell_idx(int dir, int na, int nb, int a, int b)
@@ -116,81 +112,67 @@ __device__ __forceinline__ void flag_bad(const Mesh& g, long long idx)
     atomicMin((unsigned long long*)g.bad, (unsigned long long)idx);
 }
 
-// -------------------------------------------------------------- Step 1 (2-D)
+// -------------------------------------------------------------- Steps 1-2 (2-D)
+// Step 1 of one cell (a, b) of direction dir: the tangential ASE-DFF
+// reconstruction from the five cells b-2..b+2, evaluated at the M Gauss lines
+// -> res (line averages; FP32 bulk: lo + the increment over the cell's hi);
+// hi: the cell's average (FP32 bulk: its high part).  For the cells whose
+// faces this stage evaluates (core), also the tangential r5 DFF (AT, Step 3),
+// the tangential differences of hi (TD, FP32 bulk) and the packed DFF of the
+// normal stencil (dn, Step 2).
 template <int M, typename R, bool WALLS>
-__global__ void __launch_bounds__(256) k_lines(Work w, int stage)
+__device__ __forceinline__ void step1_cell(const Mesh& g, const R* S, int dir, int na, int nb, int a, int b, double tb,
+                                           const double* SX, const double* SY, bool core, R res[M][4], R hi[4],
+                                           R dn[4])
 {
-    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
-         gi += (long long)gridDim.x * blockDim.x) {
-        int k = find_mesh(w, gi);
-        const Mesh& g = w.mesh[k];
-        // local indices in 32 bits (the host bounds a mesh's work items below 2^31)
-        unsigned li = (unsigned)(gi - w.off[k]);
-        unsigned nxl = (unsigned)(g.nx + 6) * (unsigned)(g.ny + 2);
-        int dir = li < nxl ? 0 : 1;
-        if (dir == 1) li -= nxl;
-        int na, nb;
-        local_dims<M>(g, dir, na, nb);
-        int a, b;
-        if (dir == 0) { unsigned d = na + 6, q = li / d; a = (int)(li - q * d) - 3; b = (int)q - 1; }
-        else { unsigned d = nb + 2, q = li / d; b = (int)(li - q * d) - 1; a = (int)q - 3; }
-        const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
-        const double tb = WALLS ? stage_time(g, stage) : 0.0;  // inflow ghost states
-        // sigma of the DFF (Sec. 3.1): of step n-1 in both stages, or, in stage 2
-        // of the stage-lag reading, the face means of stage 1 of this step
-        const bool lag_stage = stage == 2 && g.dff_lag;
-        const double* SX = lag_stage ? g.sig_xn : g.sig_x;
-        const double* SY = lag_stage ? g.sig_yn : g.sig_y;
-        // the tangential stencil: a direct walk for interior cells, whose loads
-        // are issued before the DFF selections so that their latencies overlap
-        bool inner = a >= 0 && a < na && b >= 2 && b + 2 < nb;
-        long long P = g.plane;
-        long long ci = dir == 0 ? (long long)b * g.nx + a : (long long)a * g.nx + b;
-        long long st = dir == 0 ? g.nx : 1;  // tangential neighbour stride
-        int pt = dir == 0 ? 8 : 4;           // plane of the tangential cell slope
-        constexpr bool BULK32 = sizeof(R) == 4;
-        R sw[4][5], swt[4][5], slo[4][BULK32 ? 5 : 1];  // slo: low parts of the averages (FP32 bulk)
-        if (inner) {
+    constexpr bool BULK32 = sizeof(R) == 4;
+    // the tangential stencil: a direct walk for interior cells, whose loads
+    // are issued before the DFF selections so that their latencies overlap
+    bool inner = a >= 0 && a < na && b >= 2 && b + 2 < nb;
+    long long P = g.plane;
+    long long ci = dir == 0 ? (long long)b * g.nx + a : (long long)a * g.nx + b;
+    long long st = dir == 0 ? g.nx : 1;  // tangential neighbour stride
+    int pt = dir == 0 ? 8 : 4;           // plane of the tangential cell slope
+    R sw[4][5], swt[4][5], slo[4][BULK32 ? 5 : 1];  // slo: low parts of the averages (FP32 bulk)
+    if (inner) {
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                int gv = vglob(dir, v);
-                const R* w0 = S + gv * P + ci;
-                const R* wt = S + (pt + gv) * P + ci;
-                const R* wl = S + (12 + 8 * M + gv) * P + ci;
+        for (int v = 0; v < 4; ++v) {
+            int gv = vglob(dir, v);
+            const R* w0 = S + gv * P + ci;
+            const R* wt = S + (pt + gv) * P + ci;
+            const R* wl = S + (12 + 8 * M + gv) * P + ci;
 #pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    sw[v][q] = w0[(q - 2) * st];
-                    swt[v][q] = wt[(q - 2) * st];
-                    if (BULK32) slo[v][BULK32 ? q : 0] = wl[(q - 2) * st];
-                }
+            for (int q = 0; q < 5; ++q) {
+                sw[v][q] = w0[(q - 2) * st];
+                swt[v][q] = wt[(q - 2) * st];
+                if (BULK32) slo[v][BULK32 ? q : 0] = wl[(q - 2) * st];
             }
-        } else {
-#pragma unroll
-            for (int v = 0; v < 4; ++v)
-#pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    sw[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 0, v, 0, a, b + q - 2, tb);
-                    swt[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 2, v, 0, a, b + q - 2, tb);
-                    if (BULK32) slo[v][BULK32 ? q : 0] = lcell<2, M, R, WALLS>(g, S, dir, 5, v, 0, a, b + q - 2, tb);
-                }
         }
-        // face sigma of the tangential stencil: a direct walk for interior cells
-        double s6[6];
-        if (inner) {
-            const double* sp = dir == 0 ? SY + (long long)(b - 2) * g.nx + a
-                                        : SX + (long long)a * (g.nx + 1) + (b - 2);
-            const long long ss = dir == 0 ? g.nx : 1;
+    } else {
 #pragma unroll
-            for (int q = 0; q < 6; ++q) s6[q] = sp[q * ss];
-        } else {
+        for (int v = 0; v < 4; ++v)
 #pragma unroll
-            for (int q = 0; q < 6; ++q) s6[q] = lsigT<WALLS>(g, SX, SY, dir, a, b - 2 + q);
-        }
-        DffR<R> dff = dff_r<R>(dff_select(g.order, s6, g.thr));
-        R ht = (R)(dir == 0 ? g.dy : g.dx);
+            for (int q = 0; q < 5; ++q) {
+                sw[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 0, v, 0, a, b + q - 2, tb);
+                swt[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 2, v, 0, a, b + q - 2, tb);
+                if (BULK32) slo[v][BULK32 ? q : 0] = lcell<2, M, R, WALLS>(g, S, dir, 5, v, 0, a, b + q - 2, tb);
+            }
+    }
+    // face sigma of the tangential stencil: a direct walk for interior cells
+    double s6[6];
+    if (inner) {
+        const double* sp = dir == 0 ? SY + (long long)(b - 2) * g.nx + a : SX + (long long)a * (g.nx + 1) + (b - 2);
+        const long long ss = dir == 0 ? g.nx : 1;
+#pragma unroll
+        for (int q = 0; q < 6; ++q) s6[q] = sp[q * ss];
+    } else {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) s6[q] = lsigT<WALLS>(g, SX, SY, dir, a, b - 2 + q);
+    }
+    DffR<R> dff = dff_r<R>(dff_select(g.order, s6, g.thr));
+    R ht = (R)(dir == 0 ? g.dy : g.dx);
+    if (core) {
         long long cidx = cell_idx(dir, na, nb, a, b);
-        const long long ncell = (long long)(nb + 2) * (na + 6);  // cells of one LA plane
-        R* LA = (R*)g.LA[dir] + cidx * 4;
         // tangential r5 DFF of this cell, reused by Step 3 in k_flux
         ((R*)g.AT[dir])[cidx] = (R)dff.a[3];
         if (BULK32) {
@@ -201,150 +183,155 @@ __global__ void __launch_bounds__(256) k_lines(Work w, int stage)
             st4((R*)g.TD[dir] + cidx * 8, tdm);
             st4((R*)g.TD[dir] + cidx * 8 + 4, tdp);
         }
-        // normal-direction DFF of this cell, reused by every Gauss line in k_normal
-        if (a >= -1 && a <= na) {
-            double n6[6];
-            if (a >= 2 && a + 3 <= na && b >= 0 && b < nb) {
-                const double* sp = dir == 0 ? SX + (long long)b * (g.nx + 1) + (a - 2)
-                                            : SY + (long long)(a - 2) * g.nx + b;
-                const long long ss = dir == 0 ? 1 : g.nx;
+        // the DFF of the normal stencil, used by every Gauss line in Step 2
+        double n6[6];
+        if (a >= 2 && a + 3 <= na && b >= 0 && b < nb) {
+            const double* sp = dir == 0 ? SX + (long long)b * (g.nx + 1) + (a - 2) : SY + (long long)(a - 2) * g.nx + b;
+            const long long ss = dir == 0 ? 1 : g.nx;
 #pragma unroll
-                for (int q = 0; q < 6; ++q) n6[q] = sp[q * ss];
-            } else {
+            for (int q = 0; q < 6; ++q) n6[q] = sp[q * ss];
+        } else {
 #pragma unroll
-                for (int q = 0; q < 6; ++q) n6[q] = lsigN<2, WALLS>(g, SX, SY, dir, a - 2 + q, b);
-            }
-            R pk[4];
-            dff_pack<R>(dff_r<R>(dff_select(g.order, n6, g.thr)), pk);
-            st4((R*)g.DN[dir] + cidx * 4, pk);
+            for (int q = 0; q < 6; ++q) n6[q] = lsigN<2, WALLS>(g, SX, SY, dir, a - 2 + q, b);
         }
-        R res[M][4];
-        const R ghi = (R)g.ghi, glo = (R)g.glo, eps = (R)g.eps;
-        with_stencil<M - 2>(dff, [&](auto tag) {
-            constexpr int ST = decltype(tag)::value;
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                // FP32 bulk: differences of averages as (hi - hi) + (lo - lo), and
-                // the line average kept as lo + increment (over the cell's hi)
-                R qi = sw[v][2], dp[10];
-#pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    dp[q] = BULK32 ? (sw[v][q] - qi) + (slo[v][BULK32 ? q : 0] - slo[v][BULK32 ? 2 : 0]) : sw[v][q] - qi;
-                    dp[5 + q] = ht * swt[v][q];
-                }
-                R out[M];
-                recon_st<R, M, M - 2, ST, 6>(dff, dp, out, ghi, glo, eps);
-                const R base = BULK32 ? slo[v][BULK32 ? 2 : 0] : qi;
-#pragma unroll
-                for (int l = 0; l < M; ++l) res[l][v] = base + out[l];
-            }
-        });
-#pragma unroll
-        for (int l = 0; l < M; ++l) st4(LA + l * ncell * 4, res[l]);
+        dff_pack<R>(dff_r<R>(dff_select(g.order, n6, g.thr)), dn);
     }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) hi[v] = sw[v][2];
+    const R ghi = (R)g.ghi, glo = (R)g.glo, eps = (R)g.eps;
+    with_stencil<M - 2>(dff, [&](auto tag) {
+        constexpr int ST = decltype(tag)::value;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            // FP32 bulk: differences of averages as (hi - hi) + (lo - lo), and
+            // the line average kept as lo + increment (over the cell's hi)
+            R qi = sw[v][2], dp[10];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                dp[q] = BULK32 ? (sw[v][q] - qi) + (slo[v][BULK32 ? q : 0] - slo[v][BULK32 ? 2 : 0]) : sw[v][q] - qi;
+                dp[5 + q] = ht * swt[v][q];
+            }
+            R out[M];
+            recon_st<R, M, M - 2, ST, 6>(dff, dp, out, ghi, glo, eps);
+            const R base = BULK32 ? slo[v][BULK32 ? 2 : 0] : qi;
+#pragma unroll
+            for (int l = 0; l < M; ++l) res[l][v] = base + out[l];
+        }
+    });
 }
 
-// -------------------------------------------------------------- Step 2
-// D == 1: the cell data are the cell averages and slopes themselves.
-template <int D, int M, typename R, bool WALLS>
-__global__ void __launch_bounds__(256) k_normal(Work w, int stage)
+// Steps 1-2 of one direction, fused through shared memory.  A tile is TA x TB
+// cells (a along the face normal, b across it) of the range a in [-1, na],
+// b in [-1, nb] whose faces the stage evaluates (ghost columns and rows
+// included: Step 3 reads the face states of the rows beside the mesh).  Phase
+// 1 runs Step 1 for the tile and two halo columns on each side along a and
+// keeps each cell's M line averages, its average and the DFF of its normal
+// stencil in shared memory; phase 2 runs Step 2 (Algorithm 1) for every
+// (cell, Gauss line) of the tile from there and writes both face states.
+// The line averages never reach global memory; the halo costs 4 / TA more
+// Step 1 work.  Shared memory per CTA: (TA + 4) TB (4 M + 8) values of R,
+// launched as dynamic shared memory.  Shared-memory and thread layouts keep
+// the global x index fastest.  Work items are tiles (Work offsets count
+// tiles per mesh for the tile shape of the launch).
+template <int M, typename R, bool WALLS, int DIR>
+__global__ void __launch_bounds__(256) k_recon(Work w, int stage, int TA, int TB)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ unsigned long long cnt[4];
-    if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
-    __syncthreads();
-    constexpr int NV = D + 2;
     constexpr bool BULK32 = sizeof(R) == 4;
-    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
-         gi += (long long)gridDim.x * blockDim.x) {
-        int k = find_mesh(w, gi);
+    constexpr int NV = 4;
+    if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
+    const int TAH = TA + 4;
+    const int ncs = TAH * TB;                       // cells held per tile
+    R* s_la = (R*)smem_raw;                         // [M][ncs][4] line averages
+    R* s_hi = s_la + (size_t)M * ncs * 4;           // [ncs][4] averages (FP32 bulk: hi)
+    R* s_dn = s_hi + (size_t)ncs * 4;               // [ncs][4] packed normal DFF (tile cells)
+    const int sa = DIR == 0 ? 1 : TB;               // shared-memory stride of a
+    for (long long tile = blockIdx.x; tile < w.total; tile += gridDim.x) {
+        int k = find_mesh(w, tile);
         const Mesh& g = w.mesh[k];
-        unsigned li = (unsigned)(gi - w.off[k]);  // 32-bit local index (bounded on the host)
-        int dir = 0, na = g.nx, nb = 1;
-        if (D == 2) {
-            unsigned nxl = (unsigned)(g.nx + 2) * (unsigned)(g.ny + 2) * M;
-            dir = li < nxl ? 0 : 1;
-            if (dir == 1) li -= nxl;
-            local_dims<M>(g, dir, na, nb);
-        }
-        int l = D == 2 ? (int)(li % M) : 0;
-        unsigned r = D == 2 ? li / M : li;
-        int a, b;
-        if (D == 1) { a = (int)r - 1; b = 0; }
-        else if (dir == 0) { unsigned d = na + 2, q = r / d; a = (int)(r - q * d) - 1; b = (int)q - 1; }
-        else { unsigned d = nb + 2, q = r / d; b = (int)(r - q * d) - 1; a = (int)q - 1; }
+        int na, nb;
+        local_dims<M>(g, DIR, na, nb);
+        const int nta = (na + 2 + TA - 1) / TA;
+        const int lt = (int)(tile - w.off[k]);      // 32-bit tile index (bounded on the host)
+        const int a0 = -1 + (lt % nta) * TA, b0 = -1 + (lt / nta) * TB;
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
         const double tb = WALLS ? stage_time(g, stage) : 0.0;  // inflow ghost states
-        long long cidx = cell_idx(dir, na, nb, a, b);
-        long long lstr = dir == 0 ? 1 : (nb + 2);  // LA stride between normal neighbours
-        DffR<R> dff;
-        if (D == 2) {
+        // sigma of the DFF (Sec. 3.1): of step n-1 in both stages, or, in stage 2
+        // of the stage-lag reading, the face means of stage 1 of this step
+        const bool lag_stage = stage == 2 && g.dff_lag;
+        const double* SX = lag_stage ? g.sig_xn : g.sig_x;
+        const double* SY = lag_stage ? g.sig_yn : g.sig_y;
+        // ---- phase 1: Step 1 of the tile and its halo along a
+        for (int t = threadIdx.x; t < ncs; t += blockDim.x) {
+            int ia, ib;
+            if (DIR == 0) { ib = t / TAH; ia = t - ib * TAH; }
+            else { ia = t / TB; ib = t - ia * TB; }
+            const int a = a0 - 2 + ia, b = b0 + ib;
+            if (a > na + 2 || b > nb) continue;     // beyond the mesh's halo
+            const bool core = ia >= 2 && ia < TA + 2 && a <= na;
+            R res[M][4], hi[4], dn[4];
+            step1_cell<M, R, WALLS>(g, S, DIR, na, nb, a, b, tb, SX, SY, core, res, hi, dn);
+#pragma unroll
+            for (int l = 0; l < M; ++l) st4(s_la + ((size_t)l * ncs + t) * 4, res[l]);
+            st4(s_hi + (size_t)t * 4, hi);
+            if (core) st4(s_dn + (size_t)t * 4, dn);
+        }
+        __syncthreads();
+        // ---- phase 2: Step 2 of every (cell, Gauss line) of the tile
+        const R hn = (R)(DIR == 0 ? g.dx : g.dy);
+        const R ih = (R)1 / hn;
+        const R ghi = (R)g.ghi, glo = (R)g.glo, eps = (R)g.eps;
+        R* FR = (R*)g.FR[DIR];
+        const long long npt = fr_npt(na, nb, M);
+        const long long P = g.plane;
+        const int nitem = TA * TB * M;
+        for (int it = threadIdx.x; it < nitem; it += blockDim.x) {
+            const int l = it % M, c = it / M;
+            int ia, ib;
+            if (DIR == 0) { ib = c / TA; ia = c - ib * TA + 2; }
+            else { ia = c / TB + 2; ib = c - (ia - 2) * TB; }
+            const int a = a0 - 2 + ia, b = b0 + ib;
+            if (a > na || b > nb) continue;
+            const int tc = DIR == 0 ? ib * TAH + ia : ia * TB + ib;
             R pk[4];
-            ld4((const R*)g.DN[dir] + cidx * 4, pk);
-            dff = dff_unpack<R>(pk);
-        } else {
-            double s6[6];
+            ld4(s_dn + (size_t)tc * 4, pk);
+            DffR<R> dff = dff_unpack<R>(pk);
+            {
+                // branch counts, aggregated per warp
+                int bi = dff.st < 0 ? 0 : dff.st - ST_R5 + 1;
+                unsigned act = __activemask();
+                unsigned same = __match_any_sync(act, bi);
+                if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&cnt[bi], (unsigned long long)__popc(same));
+            }
+            // the line averages and averages of the five stencil cells on this line
+            R la5[5][4], sh[5][4];
 #pragma unroll
-            // sigma of the DFF: step n-1, or in stage 2 of the stage-lag reading the
-            // face means of stage 1 of this step
-            const double* SX = (stage == 2 && g.dff_lag) ? g.sig_xn : g.sig_x;
-            for (int q = 0; q < 6; ++q) s6[q] = sigx<1, WALLS>(g, SX, a - 2 + q, 0);
-            dff = dff_r<R>(dff_select(g.order, s6, g.thr));
-        }
-        {
-            // branch counts, aggregated per warp
-            int bi = dff.st < 0 ? 0 : dff.st - ST_R5 + 1;
-            unsigned act = __activemask();
-            unsigned same = __match_any_sync(act, bi);
-            if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&cnt[bi], (unsigned long long)__popc(same));
-        }
-        R hn = (R)(dir == 0 ? g.dx : g.dy);
-        R* FR = (R*)g.FR[dir];
-        // the line averages of the five stencil cells on this Gauss line
-        R la5[5][4];
-        if (D == 2) {
-            const R* la = (const R*)g.LA[dir] + ((long long)l * (nb + 2) * (na + 6) + cidx) * 4;
-#pragma unroll
-            for (int q = 0; q < 5; ++q) ld4(la + (q - 2) * lstr * 4, la5[q]);
-        }
-        R sideL[3][4], sideR[3][4];
-        // the normal stencil of line slopes: a direct walk for interior cells
-        bool inner = D == 2 && a >= 2 && a + 2 < na && b >= 0 && b < nb;
-        long long P = g.plane;
-        long long ci = dir == 0 ? (long long)b * g.nx + a : (long long)a * g.nx + b;
-        long long sn = dir == 0 ? 1 : g.nx;                    // normal neighbour stride
-        int pl0 = (dir == 0 ? 12 : 12 + 4 * M) + 4 * l;         // first line-slope plane of line l
-        // all line slopes of the stencil are loaded before the first
-        // reconstruction, so their latencies overlap
-        R sl[D == 2 ? NV : 1][5];
-        // FP32 bulk: the high parts of the five cell averages along the normal,
-        // whose differences join those of the line averages' increments
-        R sh[D == 2 && BULK32 ? NV : 1][5];
-        if (D == 2) {
+            for (int q = 0; q < 5; ++q) {
+                ld4(s_la + ((size_t)l * ncs + tc + (q - 2) * sa) * 4, la5[q]);
+                ld4(s_hi + (size_t)(tc + (q - 2) * sa) * 4, sh[q]);
+            }
+            // the normal stencil of line slopes: a direct walk for interior cells
+            const bool inner = a >= 2 && a + 2 < na && b >= 0 && b < nb;
+            const long long ci = DIR == 0 ? (long long)b * g.nx + a : (long long)a * g.nx + b;
+            const long long sn = DIR == 0 ? 1 : g.nx;                  // normal neighbour stride
+            const int pl0 = (DIR == 0 ? 12 : 12 + 4 * M) + 4 * l;       // first line-slope plane of line l
+            R sl[NV][5];
             if (inner) {
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    const R* ws = S + (pl0 + vglob(dir, v)) * P + ci;
-                    const R* wh = S + vglob(dir, v) * P + ci;
+                    const R* ws = S + (pl0 + vglob(DIR, v)) * P + ci;
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) {
-                        sl[v][q] = ws[(q - 2) * sn];
-                        if (BULK32) sh[BULK32 ? v : 0][q] = wh[(q - 2) * sn];
-                    }
+                    for (int q = 0; q < 5; ++q) sl[v][q] = ws[(q - 2) * sn];
                 }
             } else {
 #pragma unroll
                 for (int v = 0; v < NV; ++v)
 #pragma unroll
-                    for (int q = 0; q < 5; ++q) {
-                        sl[v][q] = lcell<2, M, R, WALLS>(g, S, dir, 3, v, l, a + q - 2, b, tb);
-                        if (BULK32) sh[BULK32 ? v : 0][q] = lcell<2, M, R, WALLS>(g, S, dir, 0, v, 0, a + q - 2, b, tb);
-                    }
+                    for (int q = 0; q < 5; ++q) sl[v][q] = lcell<2, M, R, WALLS>(g, S, DIR, 3, v, l, a + q - 2, b, tb);
             }
-        }
-        const R ghi = (R)g.ghi, glo = (R)g.glo, eps = (R)g.eps;
-        const R ih = (R)1 / hn;
-        if constexpr (D == 2) {
-            with_stencil<(M >= 2 ? M - 2 : 0)>(dff, [&](auto tag) {
+            R sideL[3][4], sideR[3][4];
+            with_stencil<M - 2>(dff, [&](auto tag) {
                 constexpr int ST = decltype(tag)::value;
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
@@ -354,55 +341,107 @@ __global__ void __launch_bounds__(256) k_normal(Work w, int stage)
                     R qi = la5[2][v], dp[10];
 #pragma unroll
                     for (int q = 0; q < 5; ++q) {
-                        dp[q] = BULK32 ? (sh[BULK32 ? v : 0][q] - sh[BULK32 ? v : 0][2]) + (la5[q][v] - qi) : la5[q][v] - qi;
+                        dp[q] = BULK32 ? (sh[q][v] - sh[2][v]) + (la5[q][v] - qi) : la5[q][v] - qi;
                         dp[5 + q] = hn * sl[v][q];
                     }
                     R out[6];
-                    recon_st<R, 6, (M >= 2 ? M - 2 : 0), ST, 0>(dff, dp, out, ghi, glo, eps);
+                    recon_st<R, 6, M - 2, ST, 0>(dff, dp, out, ghi, glo, eps);
                     // FP32 bulk: the left state of face a+1 over the hi of that face's
                     // right cell a+1, like the right state: a face's two states share a base
-                    const R shift = BULK32 ? sh[BULK32 ? v : 0][2] - sh[BULK32 ? v : 0][3] : (R)0;
+                    const R shift = BULK32 ? sh[2][v] - sh[3][v] : (R)0;
                     sideL[0][v] = (qi + shift) + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
                     sideR[0][v] = qi + out[3]; sideR[1][v] = out[4] * ih; sideR[2][v] = out[5] * ih * ih;
                 }
             });
-        } else {
+            // side 0: left state of face a+1 (value at xi = +1/2)
+            if (a + 1 <= na) {
+                long long pt = fr_row(DIR, na, nb, b + 1, a + 1) * M + l;
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                // FP32 bulk: differences as (hi - hi) + (lo - lo); the face values
-                // come out as increments over this cell's hi (qi = lo)
-                R qi = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a, 0, tb);
-                R ql = BULK32 ? cell<1, 1, R, WALLS>(g, S, 5, v, 0, a, 0, tb) : (R)0;
-                R dp[10];
+                for (int nd = 0; nd < 3; ++nd) st4(FR + fr_off(npt, pt, 0, nd), sideL[nd]);
+            }
+            // side 1: right state of face a (value at xi = -1/2)
+            if (a >= 0) {
+                long long pt = fr_row(DIR, na, nb, b + 1, a) * M + l;
 #pragma unroll
-                for (int q = 0; q < 5; ++q) {
-                    dp[q] = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a + q - 2, 0, tb) - qi;
-                    if (BULK32) dp[q] += cell<1, 1, R, WALLS>(g, S, 5, v, 0, a + q - 2, 0, tb) - ql;
-                    dp[5 + q] = hn * cell<1, 1, R, WALLS>(g, S, 1, v, 0, a + q - 2, 0, tb);
-                }
-                // the left state of face a+1 over hi of cell a+1 (a face's states share a base)
-                const R shift = BULK32 ? qi - cell<1, 1, R, WALLS>(g, S, 0, v, 0, a + 1, 0, tb) : (R)0;
-                if (BULK32) qi = ql;
-                R out[6];
-                recon<R, 6>(dff, g.oi, 0, dp, out, ghi, glo, eps);
-                sideL[0][v] = (qi + shift) + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
-                sideR[0][v] = qi + out[3]; sideR[1][v] = out[4] * ih; sideR[2][v] = out[5] * ih * ih;
+                for (int nd = 0; nd < 3; ++nd) st4(FR + fr_off(npt, pt, 1, nd), sideR[nd]);
             }
         }
-        if (D == 1) {
+        __syncthreads();  // the next tile reuses the shared memory
+    }
+    if (threadIdx.x < 4 && cnt[threadIdx.x] && w.n > 0) atomicAdd(&w.mesh[0].branch[threadIdx.x], cnt[threadIdx.x]);
+}
+
+// -------------------------------------------------------------- Step 2 (1-D)
+// The reconstruction of a 1-D cell a in [-1, nx] from the cell averages and
+// slopes of a-2..a+2: the right state of face a and the left state of face a+1.
+template <typename R, bool WALLS>
+__global__ void __launch_bounds__(256) k_normal1(Work w, int stage)
+{
+    __shared__ unsigned long long cnt[4];
+    if (threadIdx.x < 4) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    constexpr int NV = 3;
+    constexpr bool BULK32 = sizeof(R) == 4;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
+         gi += (long long)gridDim.x * blockDim.x) {
+        int k = find_mesh(w, gi);
+        const Mesh& g = w.mesh[k];
+        const int a = (int)(gi - w.off[k]) - 1;
+        const int na = g.nx;
+        const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
+        const double tb = WALLS ? stage_time(g, stage) : 0.0;  // inflow ghost states
+        double s6[6];
+        // sigma of the DFF: step n-1, or in stage 2 of the stage-lag reading the
+        // face means of stage 1 of this step
+        const double* SX = (stage == 2 && g.dff_lag) ? g.sig_xn : g.sig_x;
 #pragma unroll
-            for (int nd = 0; nd < 3; ++nd) { sideL[nd][3] = (R)0; sideR[nd][3] = (R)0; }
+        for (int q = 0; q < 6; ++q) s6[q] = sigx<1, WALLS>(g, SX, a - 2 + q, 0);
+        DffR<R> dff = dff_r<R>(dff_select(g.order, s6, g.thr));
+        {
+            // branch counts, aggregated per warp
+            int bi = dff.st < 0 ? 0 : dff.st - ST_R5 + 1;
+            unsigned act = __activemask();
+            unsigned same = __match_any_sync(act, bi);
+            if ((int)(threadIdx.x & 31) == __ffs(same) - 1) atomicAdd(&cnt[bi], (unsigned long long)__popc(same));
         }
-        const long long npt = fr_npt(na, nb, M);
+        const R hn = (R)g.dx;
+        const R ih = (R)1 / hn;
+        const R ghi = (R)g.ghi, glo = (R)g.glo, eps = (R)g.eps;
+        R sideL[3][4], sideR[3][4];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            // FP32 bulk: differences as (hi - hi) + (lo - lo); the face values
+            // come out as increments over this cell's hi (qi = lo)
+            R qi = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a, 0, tb);
+            R ql = BULK32 ? cell<1, 1, R, WALLS>(g, S, 5, v, 0, a, 0, tb) : (R)0;
+            R dp[10];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                dp[q] = cell<1, 1, R, WALLS>(g, S, 0, v, 0, a + q - 2, 0, tb) - qi;
+                if (BULK32) dp[q] += cell<1, 1, R, WALLS>(g, S, 5, v, 0, a + q - 2, 0, tb) - ql;
+                dp[5 + q] = hn * cell<1, 1, R, WALLS>(g, S, 1, v, 0, a + q - 2, 0, tb);
+            }
+            // the left state of face a+1 over hi of cell a+1 (a face's states share a base)
+            const R shift = BULK32 ? qi - cell<1, 1, R, WALLS>(g, S, 0, v, 0, a + 1, 0, tb) : (R)0;
+            if (BULK32) qi = ql;
+            R out[6];
+            recon<R, 6>(dff, g.oi, 0, dp, out, ghi, glo, eps);
+            sideL[0][v] = (qi + shift) + out[0]; sideL[1][v] = out[1] * ih; sideL[2][v] = out[2] * ih * ih;
+            sideR[0][v] = qi + out[3]; sideR[1][v] = out[4] * ih; sideR[2][v] = out[5] * ih * ih;
+        }
+#pragma unroll
+        for (int nd = 0; nd < 3; ++nd) { sideL[nd][3] = (R)0; sideR[nd][3] = (R)0; }
+        R* FR = (R*)g.FR[0];
+        const long long npt = fr_npt(na, 1, 1);
         // side 0: left state of face a+1 (value at xi = +1/2)
         if (a + 1 <= na) {
-            long long pt = fr_row(dir, na, nb, b + 1, a + 1) * M + l;
+            long long pt = fr_row(0, na, 1, 1, a + 1);
 #pragma unroll
             for (int nd = 0; nd < 3; ++nd) st4(FR + fr_off(npt, pt, 0, nd), sideL[nd]);
         }
         // side 1: right state of face a (value at xi = -1/2)
         if (a >= 0) {
-            long long pt = fr_row(dir, na, nb, b + 1, a) * M + l;
+            long long pt = fr_row(0, na, 1, 1, a);
 #pragma unroll
             for (int nd = 0; nd < 3; ++nd) st4(FR + fr_off(npt, pt, 1, nd), sideR[nd]);
         }

@@ -6,9 +6,11 @@
 namespace cgks {
 typedef void (*KStage)(Work, int);
 typedef void (*KOne)(Work);
+typedef void (*KTile)(Work, int, int, int);
 struct Kfns {
-    KStage lines, normal;      // instances for meshes without walls
-    KStage linesw, normalw;    // the same with the wall ghost rules
+    KTile recon[2];            // 2-D Steps 1-2 per direction (meshes without walls)
+    KTile reconw[2];           // the same with the wall ghost rules
+    KStage normal, normalw;    // 1-D Step 2, without and with the wall ghost rules
     KOne flux1, flux2, upd1, upd2, cfl, siginit, check;
     KStage convert;  // FP32-bulk state copies (to_float = 1: FP64 -> float planes)
     KOne flux1v[2], flux2v[2];  // flux variants: [0] uncapped, [1] register-capped (tau = 0)

@@ -17,10 +17,17 @@ template <int D, int M, typename R>
 Kfns make_kfns()
 {
     Kfns k;
-    k.lines = D == 2 ? (KStage)k_lines<M, R, false> : nullptr;
-    k.normal = k_normal<D, M, R, false>;
-    k.linesw = D == 2 ? (KStage)k_lines<M, R, true> : nullptr;
-    k.normalw = k_normal<D, M, R, true>;
+    if constexpr (D == 2) {
+        k.recon[0] = k_recon<M, R, false, 0>;
+        k.recon[1] = k_recon<M, R, false, 1>;
+        k.reconw[0] = k_recon<M, R, true, 0>;
+        k.reconw[1] = k_recon<M, R, true, 1>;
+        k.normal = k.normalw = nullptr;
+    } else {
+        k.recon[0] = k.recon[1] = k.reconw[0] = k.reconw[1] = nullptr;
+        k.normal = k_normal1<R, false>;
+        k.normalw = k_normal1<R, true>;
+    }
     k.flux1v[0] = k_flux<D, M, R, 1, 0, 0>;
     k.flux2v[0] = k_flux<D, M, R, 2, 0, 0>;
     k.flux1v[1] = k_flux<D, M, R, 1, 1, 0>;

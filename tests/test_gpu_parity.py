@@ -358,8 +358,10 @@ def test_autotune_keeps_results_bitwise_and_state(precision):
         if tune:
             before = s.get_state()
             choice = s.autotune()
-            assert set(choice) >= {"lines", "normal", "flux1", "update1"}
-            assert all(abs(c) in (64, 128, 256, 512) for c in choice.values())
+            assert set(choice) >= {"recon_x", "recon_y", "flux1", "update1", "tile_x", "tile_y"}
+            assert all(abs(choice[k]) in (64, 128, 256, 512)
+                       for k in ("recon_x", "recon_y", "flux1", "flux2", "update1", "update2"))
+            assert all(ta > 0 and tb > 0 for ta, tb in (choice["tile_x"], choice["tile_y"]))
             after = s.get_state()
             for f in FIELDS_2D:
                 assert np.array_equal(before[f], after[f]), f
