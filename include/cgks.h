@@ -222,7 +222,7 @@ int cgks_get_stats(cgks_solver* s, cgks_stats* st);
  * memory) are timed over tile shapes TA x TB (cells along the face normal x
  * across it: 28x8, 60x4, 12x16, 28x4, 12x8, 124x2) at 128 and 256 threads;
  * the other kernels over block sizes 64..512 (persistent grid = SM count x
- * resident blocks), the flux kernels also in a register-capped variant (more
+ * resident blocks), the FP64 flux kernels also in a register-capped variant (more
  * resident warps, some spilling).  The state is not advanced (only scratch is
  * written; the simulated time, the status word and the fallback count are
  * restored) and results do not depend on the choice: every work item is

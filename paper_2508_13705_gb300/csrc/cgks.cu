@@ -411,6 +411,7 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         g.idx = 1.0 / g.dx; g.idy = 1.0 / g.dy;
         g.mu = p->mu; g.muf = (float)p->mu;
         g.idxf = (float)g.idx; g.idyf = (float)g.idy;
+        g.idxlo = (float)(g.idx - (double)g.idxf); g.idylo = (float)(g.idy - (double)g.idyf);
         g.plane = (long long)nx[k] * ny[k];
         char* m0 = b->slab + base[k];
         g.S0 = (double*)(m0 + L[k].S);
@@ -1210,6 +1211,7 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     g.idx = 1.0 / g.dx; g.idy = 1.0;
     g.mu = p->mu; g.muf = (float)p->mu;
     g.idxf = (float)g.idx; g.idyf = 1.0f;
+    g.idxlo = (float)(g.idx - (double)g.idxf); g.idylo = 0.0f;
     g.S0 = state_out;
     g.S1 = (double*)(base + oS1);
     if (rs == 4) {

@@ -73,6 +73,7 @@ struct Mesh {
     double bcx[4][2];               // split point along the side: bcx[0] + bcx[1] t
     float muf;
     float gf, Kf, c1f, c2f, idxf, idyf;  // FP32-bulk copies (no per-point conversions)
+    float idxlo, idylo;             // low parts: idx = idxf + idxlo to float-float accuracy
     long long plane;                // nx * ny
     // state: planes of nx*ny doubles.  2-D: W[4] Wx[4] Wy[4] Wxl[m][4] Wyl[m][4];
     // 1-D: W[3] Wx[3]
@@ -91,7 +92,7 @@ struct Mesh {
                                     // of each cell, local frame, [8] floats
     double* SP[2];                  // sigma per face Gauss point
     double* dt;                     // device scalar (this mesh's step)
-    float* dtf;                     // the same in FP32
+    float* dtf;                     // the same in FP32: [0] float(dt), [1] float(dt - [0])
     double* t;                      // device scalar (simulated time)
     double* tn;                     // device scalar: t^n of the step in flight
     unsigned long long* nfall;      // face-point sides that took the fallback
@@ -369,23 +370,24 @@ __device__ __forceinline__ ff ff_div(float a, float b)
     return ff_norm(q, __fdiv_rn(__fmaf_rn(-q, b, a), b));
 }
 __device__ __forceinline__ double ff_val(ff a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
 
 // Euler flux along the local normal of a state given by floats (rho, m_n,
 // m_t, E) (2-D, D = 2) or (rho, m, E) (1-D), in float-float: (m_n, m_n u + p,
 // m_t u, u (E + p)) with u = m_n / rho, p = (gamma - 1)(E - (m_n u + m_t v) / 2).
 // gm1 = gamma - 1 as a float-float.
 template <int D>
-__device__ __forceinline__ void euler_flux_ff(const float* w, ff gm1, double* F)
+__device__ __forceinline__ void euler_flux_ff(const float* w, ff gm1, ff* F)
 {
     const float rho = w[0], mn = w[1], mt = D == 2 ? w[2] : 0.0f, E = w[D + 1];
     ff u = ff_div(mn, rho);
     ff v = ff_div(mt, rho);
     ff ke = ff_add(ff_mul(ff_of(mn), u), ff_mul(ff_of(mt), v));  // rho |U|^2
     ff p = ff_mul(gm1, ff_add(ff_of(E), ff_mul(ff_of(-0.5f), ke)));
-    F[0] = (double)mn;
-    F[1] = ff_val(ff_add(ff_mul(ff_of(mn), u), p));
-    if (D == 2) F[2] = ff_val(ff_mul(ff_of(mt), u));
-    F[D + 1] = ff_val(ff_mul(u, ff_add(ff_of(E), p)));
+    F[0] = ff_of(mn);
+    F[1] = ff_add(ff_mul(ff_of(mn), u), p);
+    if (D == 2) F[2] = ff_mul(ff_of(mt), u);
+    F[D + 1] = ff_mul(u, ff_add(ff_of(E), p));
 }
 
 // F(w0 + q) - F(w0) of the Euler flux along the local normal, by algebra in

@@ -457,8 +457,10 @@ __global__ void __launch_bounds__(256) k_normal1(Work w, int stage)
 // into the kinetic weighting Q0, dQ0 (Eq. 2.7) and the half-range terms of
 // Eq. 2.6 as soon as they are formed, so only one side is live at a time.
 // CAP = 1 asks for at least 4 resident blocks of 128 threads (<= 128 registers,
-// spilling the rest); CAP = 0 for 3 in FP32 (<= 170 registers, no spills) and
-// 1 in FP64.  The autotuner times both variants.  HG = 1 compiles the
+// spilling the rest); CAP = 0 for 3 in FP32 (<= 170 registers) and 1 in FP64.
+// The autotuner times both variants in FP64, where they round alike; the
+// FP32-bulk form has the uncapped one only (a capped compilation may contract
+// its FP32 arithmetic differently, and results must not depend on tuning).  HG = 1 compiles the
 // collision-time terms (tau > 0); the tau = 0 instance leaves them out and
 // carries fewer live values.  PF = true compiles the first-order fallback at
 // face points whose reconstructed state is not physical (a flagged option).
@@ -517,11 +519,8 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         // face's right cell f is the base of both face states (local frame)
         const R* SF = state_planes<R>(g, STAGE == 1 ? 0 : 1);
         const double tb = stage_time(g, STAGE);
-        // W_l - W_r as the difference of the two increments, and whether it is
-        // small enough for the kinetic weighting to be taken to first order in
-        // it (below); hb1: hi of the right cell f
-        R hb1[4] = {0, 0, 0, 0}, dW[4] = {0, 0, 0, 0}, Dl[4] = {0, 0, 0, 0};
-        bool lin = false;
+        // hb1: hi of the right cell f, the base of both face states
+        R hb1[4] = {0, 0, 0, 0};
         if (BULK32) {
             if (f < na && (D == 1 || b < nb)) {
                 long long ci = dir == 0 ? (long long)b * g.nx + f : (long long)f * g.nx + b;
@@ -531,17 +530,13 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
 #pragma unroll
                 for (int v = 0; v < NV; ++v) hb1[v] = lcell<D, M, R, true>(g, SF, dir, 0, v, 0, f, b, tb);
             }
-            R e0[4], e1[4];
-            ld4(FR + (p00 + rs + l) * 8, e0);
-            ld4(FR + npt * 12 + (p00 + rs + l) * 8, e1);
-            R sc = fabs(hb1[0]) + fabs(hb1[NV - 1]);
-            lin = true;
-#pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                dW[v] = e0[v] - e1[v];
-                lin &= fabs(dW[v]) <= (R)2.5e-4 * sc;
-            }
         }
+        // FP32 bulk: whether the jump W_l - W_r is small enough for the kinetic
+        // weighting to be taken to first order in it (decided with the left
+        // state, below); the first-order term, held in Q0 itself unless the
+        // point fallback may still change the states
+        bool lin = false;
+        R Dl[4] = {0, 0, 0, 0};
         R e1v[4] = {1, 0, 0, 0};
         R Q0[4] = {0, 0, 0, 0};
         R dQ[ND][4];
@@ -554,69 +549,27 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         bool bad = false, ok = true;
 #pragma unroll 1
         for (int side = 0; side < 2; ++side) {
-            // Step 2 data: W, W_n, W_nn (FP32 bulk: W as an increment over hb1)
-            R d[6][4];
+            // Step 2 data: W, W_n, W_nn (FP32 bulk: W as an increment over hb1);
+            // Step 3's tangential derivatives are formed later, right before
+            // their micro-slope solves, so that few derivatives are live at once
+            R d0[4], dn[2][4];
             const int a = side == 0 ? f - 1 : f;  // the reconstructing cell
             const R* Fs = FR + side * npt * 12 + p00 * 8;  // (W, W_n) of segment b - 1
-            ld4(Fs + (rs + l) * 8, d[0]);
-            ld4(Fs + (rs + l) * 8 + 4, d[1]);
-            ld4(FR + side * npt * 12 + npt * 8 + (p00 + rs + l) * 4, d[2]);
-            if (D == 2) {
-                // Step 3: tangential derivatives from the 3M face points of
-                // segments b-1, b, b+1, scaled by the tangential r5 DFF of the
-                // reconstructing cell (a = f-1 for the left state, f for the right)
-                R at = ((const R*)g.AT[dir])[cell_idx(dir, na, nb, a, b)];
-                R iht = (R)1 / (R)(dir == 0 ? g.dy : g.dx);
-                R c1 = at * iht, c2 = at * iht * iht;
-                R wt[4] = {0, 0, 0, 0}, wtt[4] = {0, 0, 0, 0}, wnt[4] = {0, 0, 0, 0};
-#pragma unroll
-                for (int s = 0; s < 3; ++s)
-#pragma unroll
-                    for (int kk = 0; kk < M; ++kk) {
-                        const R* q = Fs + (s * rs + kk) * 8;
-                        R x0[4], x1[4];
-                        ld4(q, x0);
-                        ld4(q + 4, x1);
-                        R w1 = s_d1[l][s * M + kk], w2 = s_d2[l][s * M + kk];
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            wt[v] += w1 * x0[v];
-                            wtt[v] += w2 * x0[v];
-                            wnt[v] += w1 * x1[v];
-                        }
-                    }
-                if (BULK32) {
-                    // the segment points' values are increments over hi of the
-                    // right cells (f, b-1), (f, b), (f, b+1): add the bases' part
-                    // from their differences (the weights of a constant sum to zero)
-                    R dm[4], dpl[4];
-                    const R* td = (const R*)g.TD[dir] + cell_idx(dir, na, nb, f, b) * 8;
-                    ld4(td, dm);
-                    ld4(td + 4, dpl);
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        wt[v] += s_c1[l][0] * dm[v] + s_c1[l][2] * dpl[v];
-                        wtt[v] += s_c2[l][0] * dm[v] + s_c2[l][2] * dpl[v];
-                    }
-                }
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    d[3][v] = c1 * wt[v];
-                    d[4][v] = c2 * wtt[v];
-                    d[5][v] = c1 * wnt[v];
-                }
-            }
+            ld4(Fs + (rs + l) * 8, d0);
+            ld4(Fs + (rs + l) * 8 + 4, dn[0]);
+            ld4(FR + side * npt * 12 + npt * 8 + (p00 + rs + l) * 4, dn[1]);
             // the side's state
             R ws[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) ws[v] = BULK32 ? hb1[v] + d[0][v] : d[0][v];
+            for (int v = 0; v < 4; ++v) ws[v] = BULK32 ? hb1[v] + d0[v] : d0[v];
+            bool fb = false;  // the side fell back to its cell average (all derivatives zero)
             if (PF) {
                 // fallback: a side whose point state has rho <= 0 or p <= 0 takes
                 // the average of the cell it was reconstructed from, first order;
                 // the test is made in FP64 (FP32 bulk: on hi + increment)
                 double W4[4];
 #pragma unroll
-                for (int v = 0; v < 4; ++v) W4[v] = BULK32 ? (double)hb1[v] + (double)d[0][v] : (double)d[0][v];
+                for (int v = 0; v < 4; ++v) W4[v] = BULK32 ? (double)hb1[v] + (double)d0[v] : (double)d0[v];
                 double rho = W4[0];
                 double m2 = W4[1] * W4[1] + (D == 2 ? W4[2] * W4[2] : 0.0);
                 double p = (g.gamma - 1.0) * (W4[NV - 1] - 0.5 * m2 / rho);
@@ -625,14 +578,14 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
                     for (int v = 0; v < NV; ++v) {
                         // FP32 bulk: the average over hb1, (hi_a - hb1) + lo_a
                         if (BULK32)
-                            d[0][v] = (side == 0 ? lcell<D, M, R, true>(g, SF, dir, 0, v, 0, a, b, tb) - hb1[v] : (R)0)
-                                    + lcell<D, M, R, true>(g, SF, dir, 5, v, 0, a, b, tb);
+                            d0[v] = (side == 0 ? lcell<D, M, R, true>(g, SF, dir, 0, v, 0, a, b, tb) - hb1[v] : (R)0)
+                                  + lcell<D, M, R, true>(g, SF, dir, 5, v, 0, a, b, tb);
                         else
-                            d[0][v] = lcell<D, M, R, true>(g, SF, dir, 0, v, 0, a, b, tb);
-                        ws[v] = BULK32 ? hb1[v] + d[0][v] : d[0][v];
-#pragma unroll
-                        for (int q = 1; q < 6; ++q) d[q][v] = (R)0;
+                            d0[v] = lcell<D, M, R, true>(g, SF, dir, 0, v, 0, a, b, tb);
+                        ws[v] = BULK32 ? hb1[v] + d0[v] : d0[v];
+                        dn[0][v] = dn[1][v] = (R)0;
                     }
+                    fb = true;
                     lin = false;  // the states changed: weight them directly
                     atomicAdd(g.nfall, 1ull);
                 }
@@ -657,36 +610,115 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
             gram<R, D, 0, 0>(Ms, Gs);
             R t[4], z[4];
             grow0<R, D>(Gs, Ms.rho, t);
-#pragma unroll
-            for (int v = 0; v < NV; ++v) Q0[v] += t[v];
-            if (BULK32 && side == 0 && lin) {
+            if (BULK32 && side == 0) {
                 // Q0 = W_r + (H(W_l) - H(W_r)), H the u > 0 half-range moments;
                 // for a small jump, H(W_l) - H(W_r) = dH/dW (W_l - W_r) to second
                 // order, where dH/dW dW = <psi a>_{u > 0} with <a> = dW: the
-                // rounding then stays relative to the jump
-                R aa[4];
-                slope<R, D>(Ms, K, dW, aa);
-                gmul<R, D>(Gs, aa, Ms.rho, Dl);
+                // rounding then stays relative to the jump.  W_l - W_r is the
+                // difference of the two increments (a face's states share a base).
+                R e1[4], dW[4];
+                ld4(FR + npt * 12 + (p00 + rs + l) * 8, e1);
+                const R sc = fabs(hb1[0]) + fabs(hb1[NV - 1]);
+                lin = true;
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    dW[v] = d0[v] - e1[v];
+                    lin &= fabs(dW[v]) <= (R)2.5e-4 * sc;
+                }
+                if (NV < 4) dW[3] = (R)0;
+                if (lin) {
+                    R aa[4];
+                    slope<R, D>(Ms, K, dW, aa);
+                    gmul<R, D>(Gs, aa, Ms.rho, PF ? Dl : Q0);
+                }
+            }
+            if (!(BULK32 && lin && !PF)) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v) Q0[v] += t[v];
             }
             if (hgks) {
                 mom<R, D>(Ms, e1v, 1, 0, t);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) T5[v] += Ms.rho * t[v];
             }
-#pragma unroll
-            for (int q = 0; q < ND; ++q) {
+            // one derivative: its micro-slope (<a> = dW of this side, Eq. 2.8)
+            // into the weighted derivative dQ[q], and for q = 0 (n) and 2 (t) the
+            // half-range (a_n u + a_t v) terms of Eq. 2.6 with and without the
+            // flux's u
+            auto fold = [&](int q, const R dv[4]) {
                 R a_[4];
-                slope<R, D>(Ms, K, d[q + 1], a_);  // <a> = dW of this side (Eq. 2.8)
+                slope<R, D>(Ms, K, dv, a_);
                 gmul<R, D>(Gs, a_, Ms.rho, t);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) dQ[q][v] += t[v];
                 if (hgks && (q == 0 || (D == 2 && q == 2))) {
-                    // half-range (a_n u + a_t v) terms of Eq. 2.6, with and without the flux's u
                     int pu = q == 0 ? 1 : 0, pv = q == 0 ? 0 : 1;
                     mom<R, D>(Ms, a_, pu, pv, t);
                     mom<R, D>(Ms, a_, pu + 1, pv, z);
 #pragma unroll
                     for (int v = 0; v < NV; ++v) { S1h[v] += Ms.rho * t[v]; T6[v] += Ms.rho * z[v]; }
+                }
+            };
+            fold(0, dn[0]);
+            fold(1, dn[1]);
+            if (D == 2) {
+                // Step 3: tangential derivatives from the 3M face points of
+                // segments b-1, b, b+1, scaled by the tangential r5 DFF of the
+                // reconstructing cell (a = f-1 for the left state, f for the right)
+                R at = ((const R*)g.AT[dir])[cell_idx(dir, na, nb, a, b)];
+                R iht = (R)1 / (R)(dir == 0 ? g.dy : g.dx);
+                R c1 = fb ? (R)0 : at * iht, c2 = fb ? (R)0 : at * iht * iht;
+                {
+                    // W_t and W_tt from the points' values
+                    R wt[4] = {0, 0, 0, 0}, wtt[4] = {0, 0, 0, 0};
+#pragma unroll
+                    for (int s = 0; s < 3; ++s)
+#pragma unroll
+                        for (int kk = 0; kk < M; ++kk) {
+                            R x0[4];
+                            ld4(Fs + (s * rs + kk) * 8, x0);
+                            R w1 = s_d1[l][s * M + kk], w2 = s_d2[l][s * M + kk];
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                wt[v] += w1 * x0[v];
+                                wtt[v] += w2 * x0[v];
+                            }
+                        }
+                    if (BULK32) {
+                        // the segment points' values are increments over hi of the
+                        // right cells (f, b-1), (f, b), (f, b+1): add the bases' part
+                        // from their differences (the weights of a constant sum to zero)
+                        R dm[4], dpl[4];
+                        const R* td = (const R*)g.TD[dir] + cell_idx(dir, na, nb, f, b) * 8;
+                        ld4(td, dm);
+                        ld4(td + 4, dpl);
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            wt[v] += s_c1[l][0] * dm[v] + s_c1[l][2] * dpl[v];
+                            wtt[v] += s_c2[l][0] * dm[v] + s_c2[l][2] * dpl[v];
+                        }
+                    }
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) { wt[v] *= c1; wtt[v] *= c2; }
+                    fold(2, wt);
+                    fold(3, wtt);
+                }
+                {
+                    // W_nt from the points' normal derivatives
+                    R wnt[4] = {0, 0, 0, 0};
+#pragma unroll
+                    for (int s = 0; s < 3; ++s)
+#pragma unroll
+                        for (int kk = 0; kk < M; ++kk) {
+                            R x1[4];
+                            ld4(Fs + (s * rs + kk) * 8 + 4, x1);
+                            R w1 = s_d1[l][s * M + kk];
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) wnt[v] += w1 * x1[v];
+                        }
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) wnt[v] *= c1;
+                    fold(4, wnt);
                 }
             }
         }
@@ -698,7 +730,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
                 ld4(FR + npt * 12 + (p00 + rs + l) * 8, e1);
 #pragma unroll
                 for (int v = 0; v < NV; ++v) {
-                    qv[v] = e1[v] + Dl[v];
+                    qv[v] = e1[v] + (PF ? Dl[v] : Q0[v]);
                     Q0[v] = hb1[v] + qv[v];
                 }
             } else {
@@ -917,7 +949,7 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
         // the update still telescopes), their state parts the difference of
         // the bases' hi.
         R h0[4] = {0, 0, 0, 0}, hxn[4] = {0, 0, 0, 0}, hyn[4] = {0, 0, 0, 0};
-        double Bx[4] = {0, 0, 0, 0}, By[4] = {0, 0, 0, 0};
+        ff Bx[4], By[4];
         if (BULK32 && STAGE == 1) {
             const float* SF = g.F0;
             const double tb = *g.tn;
@@ -929,20 +961,21 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
             }
             const double gm1d = g.gamma - 1.0;
             const ff gm1 = {(float)gm1d, (float)(gm1d - (double)(float)gm1d)};
-            double f0[4], f1[4];
+            ff f0[4], f1[4];
             float wl[4];
             // x: local frame = global (rho, m_x, m_y, E)
             for (int v = 0; v < 4; ++v) wl[v] = (float)h0[v];
             euler_flux_ff<2>(wl, gm1, f0);
             for (int v = 0; v < 4; ++v) wl[v] = (float)hxn[v];
             euler_flux_ff<2>(wl, gm1, f1);
-            for (int v = 0; v < 4; ++v) Bx[v] = f1[v] - f0[v];
+            for (int v = 0; v < 4; ++v) Bx[v] = ff_add(f1[v], ff_neg(f0[v]));
             // y: local frame (rho, m_y, m_x, E), back to global order
             wl[0] = (float)h0[0]; wl[1] = (float)h0[2]; wl[2] = (float)h0[1]; wl[3] = (float)h0[3];
             euler_flux_ff<2>(wl, gm1, f0);
             wl[0] = (float)hyn[0]; wl[1] = (float)hyn[2]; wl[2] = (float)hyn[1]; wl[3] = (float)hyn[3];
             euler_flux_ff<2>(wl, gm1, f1);
-            By[0] = f1[0] - f0[0]; By[1] = f1[2] - f0[2]; By[2] = f1[1] - f0[1]; By[3] = f1[3] - f0[3];
+            const int yl[4] = {0, 2, 1, 3};
+            for (int v = 0; v < 4; ++v) By[v] = ff_add(f1[yl[v]], ff_neg(f0[yl[v]]));
         }
         R gxr0[4] = {0, 0, 0, 0}, gxl0[4] = {0, 0, 0, 0}, gyr0[4] = {0, 0, 0, 0}, gyl0[4] = {0, 0, 0, 0};
         R gxr1[4] = {0, 0, 0, 0}, gxl1[4] = {0, 0, 0, 0}, gyr1[4] = {0, 0, 0, 0}, gyl1[4] = {0, 0, 0, 0};
@@ -999,15 +1032,33 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             double Wn;
-            const double dx0 = exact_diff(gxr0[v], gxl0[v]), dy0 = exact_diff(gyr0[v], gyl0[v]);
-            if (STAGE == 1) {
-                double W = g.S0[v * P + c];
-                const double dtd = *g.dt;
-                Wn = W - (dx0 + 0.5 * dtd * Bx[v]) * idx - (dy0 + 0.5 * dtd * By[v]) * idy;  // Eq. 2.21
-                g.ACC[v * P + c] = W - (exact_diff(gxr1[v], gxl1[v]) + dtd * Bx[v]) * idx
-                                     - (exact_diff(gyr1[v], gyl1[v]) + dtd * By[v]) * idy;
+            if (BULK32) {
+                // float-float: the exact differences of the face sums (two-sums),
+                // the bases' flux differences times dt/2 or dt, over dx and dy;
+                // one conversion to FP64 per quantity (the FP64 pipe is narrow)
+                const ff ix = {g.idxf, g.idxlo}, iy = {g.idyf, g.idylo};
+                ff tx = ff_two_sum((float)gxr0[v], -(float)gxl0[v]), ty = ff_two_sum((float)gyr0[v], -(float)gyl0[v]);
+                if (STAGE == 1) {
+                    const ff hdt = {0.5f * g.dtf[0], 0.5f * g.dtf[1]}, fdt = {g.dtf[0], g.dtf[1]};
+                    tx = ff_add(tx, ff_mul(hdt, Bx[v]));
+                    ty = ff_add(ty, ff_mul(hdt, By[v]));
+                    ff ax = ff_add(ff_two_sum((float)gxr1[v], -(float)gxl1[v]), ff_mul(fdt, Bx[v]));
+                    ff ay = ff_add(ff_two_sum((float)gyr1[v], -(float)gyl1[v]), ff_mul(fdt, By[v]));
+                    double W = g.S0[v * P + c];
+                    Wn = W - ff_val(ff_add(ff_mul(tx, ix), ff_mul(ty, iy)));  // Eq. 2.21
+                    g.ACC[v * P + c] = W - ff_val(ff_add(ff_mul(ax, ix), ff_mul(ay, iy)));
+                } else {
+                    Wn = g.ACC[v * P + c] - ff_val(ff_add(ff_mul(tx, ix), ff_mul(ty, iy)));  // Eq. 2.22-2.23
+                }
             } else {
-                Wn = g.ACC[v * P + c] - dx0 * idx - dy0 * idy;  // Eq. 2.22-2.23
+                const double dx0 = exact_diff(gxr0[v], gxl0[v]), dy0 = exact_diff(gyr0[v], gyl0[v]);
+                if (STAGE == 1) {
+                    double W = g.S0[v * P + c];
+                    Wn = W - dx0 * idx - dy0 * idy;  // Eq. 2.21
+                    g.ACC[v * P + c] = W - exact_diff(gxr1[v], gxl1[v]) * idx - exact_diff(gyr1[v], gyl1[v]) * idy;
+                } else {
+                    Wn = g.ACC[v * P + c] - dx0 * idx - dy0 * idy;  // Eq. 2.22-2.23
+                }
             }
             // the FP32-bulk stage 2 reads W* from the float planes only
             if (!BULK32 || STAGE == 2) out[v * P + c] = Wn;
@@ -1085,10 +1136,10 @@ __global__ void __launch_bounds__(256) k_update1(Work w)
             }
             const double gm1d = g.gamma - 1.0;
             const ff gm1 = {(float)gm1d, (float)(gm1d - (double)(float)gm1d)};
-            double f0[3], f1[3];
+            ff f0[3], f1[3];
             euler_flux_ff<1>(h0, gm1, f0);
             euler_flux_ff<1>(h1, gm1, f1);
-            for (int v = 0; v < 3; ++v) B[v] = f1[v] - f0[v];
+            for (int v = 0; v < 3; ++v) B[v] = ff_val(ff_add(f1[v], ff_neg(f0[v])));
         }
         for (int v = 0; v < 3; ++v) {
             double Wn, Sn;
@@ -1221,7 +1272,8 @@ __global__ void k_dt(Mesh* meshes, int n, int use_cfl, const double* fixed)
             dt = fixed[k];
         }
         *g.dt = dt;
-        *g.dtf = (float)dt;
+        g.dtf[0] = (float)dt;
+        g.dtf[1] = (float)(dt - (double)g.dtf[0]);
         *g.tn = *g.t;
         *g.t += dt;
         for (int q = 0; q < 4; ++q) g.branch[q] = 0ull;  // counts cover the latest step

@@ -30,12 +30,22 @@ Kfns make_kfns()
     }
     k.flux1v[0] = k_flux<D, M, R, 1, 0, 0>;
     k.flux2v[0] = k_flux<D, M, R, 2, 0, 0>;
-    k.flux1v[1] = k_flux<D, M, R, 1, 1, 0>;
-    k.flux2v[1] = k_flux<D, M, R, 2, 1, 0>;
     k.flux1h[0] = k_flux<D, M, R, 1, 0, 1>;
     k.flux2h[0] = k_flux<D, M, R, 2, 0, 1>;
-    k.flux1h[1] = k_flux<D, M, R, 1, 1, 1>;
-    k.flux2h[1] = k_flux<D, M, R, 2, 1, 1>;
+    // the register-capped variants round exactly like the uncapped ones in
+    // FP64 only (the compiler may contract the FP32 arithmetic differently),
+    // so the FP32-bulk form offers the autotuner one variant
+    if constexpr (sizeof(R) == 8) {
+        k.flux1v[1] = k_flux<D, M, R, 1, 1, 0>;
+        k.flux2v[1] = k_flux<D, M, R, 2, 1, 0>;
+        k.flux1h[1] = k_flux<D, M, R, 1, 1, 1>;
+        k.flux2h[1] = k_flux<D, M, R, 2, 1, 1>;
+    } else {
+        k.flux1v[1] = k.flux1v[0];
+        k.flux2v[1] = k.flux2v[0];
+        k.flux1h[1] = k.flux1h[0];
+        k.flux2h[1] = k.flux2h[0];
+    }
     k.flux1p = k_flux<D, M, R, 1, 0, 1, true>;
     k.flux2p = k_flux<D, M, R, 2, 0, 1, true>;
     k.flux1 = k.flux1v[0];
