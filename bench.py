@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-config3", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the orders, 4096^2 and Shu-Osher blocks")
     ap.add_argument("--cpu-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--profile-case", choices=["fp32", "fp64"], default=None,
                     help="run one warm-up step and one step kernel by kernel on the --n vortex in the "
@@ -312,6 +313,10 @@ def main():
         line["batch"] = batch_bench(torch, cgks, stream, p32)
     if extras and not a.no_config3:
         line["config3"] = config3_bench(torch, cgks, stream)
+    if extras and not a.no_configs:
+        line["orders"] = orders_bench(torch, cgks, stream, a)
+        line["quadrants_4096"] = quadrants_bench(torch, cgks, stream)
+        line["shu_osher"] = shu_osher_bench(cgks)
     if extras and not a.no_cpu:
         line["cpu_baseline"] = cpu_baseline(order)
     # the figures a truncated log tail must still show, last
@@ -546,6 +551,90 @@ def config3_bench(torch, cgks, stream, full_order=9):
             "twenty_steps": table,
             "full_run_500_t0.6_order%d_fp32" % full_order: full,
             "note": "paper times: reconstruction only, one CPU core; GPU times: whole steps incl. CFL"}
+
+
+def orders_bench(torch, cgks, stream, a, n=2048):
+    """The vortex workload at 2048^2 at orders 5, 7 and 9, both forms (C3):
+    device time per step over a few CFL steps after the autotuner."""
+    from paper_2508_13705_gb300 import inputs
+    out = {"mesh": [n, n]}
+    for order in (5, 7, 9):
+        st = inputs.cell_state_2d(inputs.vortex_prim(), n, n, (0.0, 10.0, 0.0, 10.0), order, nq=4)
+        row = {}
+        for name, prec, k in (("fp32", cgks.FP32_BULK, 10), ("fp64", cgks.FP64, 2)):
+            s, ms, rc, tuned, prof = timed_form(torch, cgks, st, n, order, prec, k, 2, stream, None)
+            s.close()
+            row[name] = {"value": round(n * n * 2 * k / (ms / 1e3) / 1e6, 3), "ms_per_step": round(ms / k, 4),
+                         "steps": k, "status": rc}
+        out["order%d" % order] = row
+    out["unit"] = "Mcell-stage/s"
+    return out
+
+
+def quadrants_bench(torch, cgks, stream, n=4096, order=9, steps=5):
+    """C4: the seeded four-quadrant Riemann problem on [0,1]^2 at 4096^2, order
+    9 with the DFF active, HGKS tau, transmissive, FP32 bulk: device time per
+    CFL step and the branch counts of Algorithm 1 in the last step."""
+    from paper_2508_13705_gb300 import inputs
+    st = inputs.quadrants_2d(n, order, seed=0)
+    s = cgks.Solver(2, order, n, n, extent=(0.0, 1.0, 0.0, 1.0), precision=cgks.FP32_BULK,
+                    tau_mode=cgks.TAU_HGKS, bc=(1, 1, 1, 1), stream=stream.cuda_stream)
+    s.set_state(*st)
+    s.autotune()
+    s.advance(2, 0.0)
+    s.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s.advance(steps, 0.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _, rc, _ = s.sync(raise_on_error=False)
+    stats = s.stats()
+    s.close()
+    return {"workload": "four quadrants (seed 0), [0,1]^2, %dx%d, order %d, HGKS tau, transmissive, FP32 bulk"
+                        % (n, n, order),
+            "value": round(n * n * 2 * steps / (ms / 1e3) / 1e6, 3), "unit": "Mcell-stage/s",
+            "ms_per_step": round(ms / steps, 3), "steps": steps, "status": rc,
+            "branches_last_step": stats["branch"], "t": stats["t"]}
+
+
+SHU_OSHER_REF = os.path.join(ROOT, "tests", "golden", "shu_osher_t1.8_rho_1600.txt")
+
+
+def shu_osher_bench(cgks):
+    """C2: the Shu-Osher problem (Sec. 4.3) to t = 1.8 on 400 and 1600 cells,
+    orders 7 and 9, both forms: L1 density error against the 12800-cell oracle
+    reference (tests/golden, averaged onto 1600 cells; onto 400 by groups of 4)."""
+    from paper_2508_13705_gb300 import inputs
+    if not os.path.exists(SHU_OSHER_REF):
+        return {"unavailable": "reference file missing"}
+    ref1600 = np.loadtxt(SHU_OSHER_REF)
+    rows = []
+    for N in (400, 1600):
+        ref = ref1600.reshape(N, -1).mean(axis=1)
+        for order in (7, 9):
+            row = {"N": N, "order": order}
+            for name, prec in (("fp64", cgks.FP64), ("fp32", cgks.FP32_BULK)):
+                W, Wx, ghost = inputs.shu_osher_1d(N)
+                s = cgks.Solver(1, order, N, extent=(-5.0, 5.0, 0.0, 1.0), precision=prec, tau_mode=cgks.TAU_HGKS,
+                                bc=(cgks.BC_TRANSMISSIVE, cgks.BC_FIXED, 1, 1))
+                s.set_ghost(ghost)
+                s.set_state(W, Wx)
+                t0 = time.perf_counter()
+                t, steps, rc = s.run_to(1.8, max_steps=100000)
+                wall = time.perf_counter() - t0
+                rho = s.get_state()["W"][0, 0]
+                s.close()
+                row["l1_" + name] = float(np.abs(rho - ref).mean())
+                row["status_" + name] = rc
+                row["steps"] = steps
+                row["wall_s_" + name] = round(wall, 2)
+            row["fp32_over_fp64"] = row["l1_fp32"] / row["l1_fp64"]
+            rows.append(row)
+    return {"workload": "Shu-Osher, [-5,5], t = 1.8, HGKS tau, CFL 0.5; reference: oracle at 12800 cells",
+            "rows": rows}
 
 
 # ---------------------------------------------------------------- the oracle on the host cores

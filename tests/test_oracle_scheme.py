@@ -305,3 +305,37 @@ def test_stage_lag_equals_step_lag_on_smooth_data():
             o.step(2e-3)
         res.append(o.W.copy())
     assert np.array_equal(res[0], res[1])
+
+
+def _blast(N=400, cfl=0.5, **kw):
+    g = 1.4
+    o = Oracle(1, 5, N, extent=(0, 1, 0, 1), tau_mode=TAU_HGKS, bc=(3, 3, 1, 1), gamma=g, cfl=cfl, **kw)
+    x = (np.arange(N) + 0.5) / N
+    p = np.where(x < 0.1, 1000.0, np.where(x > 0.9, 100.0, 0.01))
+    W = np.zeros((3, 1, N))
+    W[0] = 1.0
+    W[2] = p / (g - 1)
+    o.set_state(W, np.zeros((3, 1, N)))
+    return o
+
+
+@pytest.mark.parametrize("cfl,positive", [(0.5, False), (0.2, False), (0.05, True)])
+def test_blast_wave_first_step_loses_positivity_ahead_of_the_jump(cfl, positive):
+    """Sec. 4.4, Woodward-Colella (pressure ratio 1e5, reflective walls, 400
+    cells).  The paper reports a pass at CFL 0.5; under the readings of this
+    build the first step leaves the second low-pressure cell (cell 41, one
+    face ahead of the jump) with a negative pressure: in stage 2 the wave has
+    reached its left face, and the S2O4 combination weights that face's flux
+    only through the stage-2 time derivative F_t*, which a flux switching on
+    within the step does not represent.  A smaller step (CFL 0.05) keeps the
+    first step positive.  The same holds with the DFF time lag of stage 2,
+    with the collision time taken from the two cells' pressures, with the
+    literal flux integral and with larger c1 or c2 (the design notes list
+    them); none is a reading that passes."""
+    o = _blast(cfl=cfl)
+    o.step(o.compute_dt())
+    W = o.W[:, 0]
+    p = 0.4 * (W[2] - 0.5 * W[1] ** 2 / W[0])
+    assert (p.min() > 0) == positive
+    if not positive:
+        assert int(p.argmin()) == 41
