@@ -202,10 +202,12 @@ def timed_form(torch, cgks, st, n, order, precision, steps, warmup, stream, pg, 
     barrier(pg)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed_" + ("fp32" if precision == cgks.FP32_BULK else "fp64"))
     e0.record(stream)
     s.advance(steps, 0.0)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()  # lets a profiler select the timed steps
     barrier(pg)
     ms = max_over_ranks(pg, e0.elapsed_time(e1))
     _, rc, _ = s.sync(raise_on_error=False)
