@@ -45,6 +45,14 @@ ORACLE_FLOPS = {
     "cell_stage_linear": {5: 40266.1, 7: 63046.3, 9: 88703.7},
 }
 
+# What the stage-1 flux kernel (order 9, tau = 0) executes per cell, counted
+# by ncu on the 1024^2 vortex (FADD + FMUL + 2 FFMA, or the FP64
+# counterparts; dram__bytes_read.sum + dram__bytes_write.sum), for the
+# kernels as profiled in profiles/kernel_counters_vortex1024_o9.md: the pipe
+# utilisation beside the algorithmic rate, and the DRAM traffic per launch.
+FLUX1_EXECUTED = {"fp32": {"flops_per_cell": 20723.7, "dram_bytes_per_cell": 1422.0},
+                  "fp64": {"flops_per_cell": 21493.3, "dram_bytes_per_cell": 2751.0}}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -350,9 +358,15 @@ def roofline(kms, precision, order, n, p32, p64, hbm):
     alg = ORACLE_FLOPS["kinetic_point_tau0"] * pts
     peak = p32 if precision == "fp32" else p64
     ach = alg / (ms / 1e3) / 1e12
+    ex = FLUX1_EXECUTED[precision] if order == 9 else None
     out = {"bound": "alu", "kernel": "k_flux, stage 1", "achieved": round(ach, 3), "peak": round(peak, 2),
            "unit": "TFLOP/s", "frac": round(ach / peak, 4),
-           "traffic": None,
+           "traffic": None if ex is None else round(ex["dram_bytes_per_cell"] * n * n),
+           "executed": None if ex is None else {
+               "tflops": round(ex["flops_per_cell"] * n * n / (ms / 1e3) / 1e12, 3),
+               "frac": round(ex["flops_per_cell"] * n * n / (ms / 1e3) / 1e12 / peak, 4),
+               "basis": "ncu executed FP operations per cell of this kernel on the 1024^2 vortex "
+                        "(profiles/kernel_counters_vortex1024_o9.md) x n^2 / launch time"},
            "algorithmic_flops_per_launch": alg,
            "basis": "oracle operation tally of the kinetic part, %.0f per face Gauss point x %d points; "
                     "peak: measured %s FMA throughput" % (ORACLE_FLOPS["kinetic_point_tau0"], pts, precision),
