@@ -465,11 +465,16 @@ __global__ void __launch_bounds__(256) k_normal1(Work w, int stage)
 // carries fewer live values.  PF = true compiles the first-order fallback at
 // face points whose reconstructed state is not physical (a flagged option).
 template <int D, int M, typename R, int STAGE, int CAP, int HG, bool PF = false>
-__global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flux(Work w)
+__global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? (HG ? 3 : 4) : 1)) k_flux(Work w)
 {
     constexpr int NV = D + 2;
     constexpr int ND = D == 2 ? 5 : 2;  // derivatives: n, nn (, t, tt, nt)
     constexpr bool BULK32 = sizeof(R) == 4;
+    // FP32 bulk: the two sides unrolled, so that their independent chains
+    // interleave, and Step 3's segment loop rolled, which keeps the tau = 0
+    // compilation within 128 registers without spills (4 blocks of 128
+    // threads per SM; the tau > 0 ones take 168, 3 blocks)
+    constexpr int kSides = BULK32 ? 2 : 1, kSegs = BULK32 ? 1 : 3;
     // Step 3 weights in shared memory: the Gauss line differs across the lanes
     // of a warp, which would serialise constant-memory reads.  FP32 bulk also
     // keeps, per line and segment, the sum of the segment's weights, which
@@ -547,7 +552,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
         R T5[4] = {0, 0, 0, 0}, T6[4] = {0, 0, 0, 0}, S1h[4] = {0, 0, 0, 0};
         R pz[2], mn[2], mt[2];
         bool bad = false, ok = true;
-#pragma unroll 1
+#pragma unroll kSides
         for (int side = 0; side < 2; ++side) {
             // Step 2 data: W, W_n, W_nn (FP32 bulk: W as an increment over hb1);
             // Step 3's tangential derivatives are formed later, right before
@@ -671,7 +676,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
                 {
                     // W_t and W_tt from the points' values
                     R wt[4] = {0, 0, 0, 0}, wtt[4] = {0, 0, 0, 0};
-#pragma unroll
+#pragma unroll kSegs
                     for (int s = 0; s < 3; ++s)
 #pragma unroll
                         for (int kk = 0; kk < M; ++kk) {
@@ -706,7 +711,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? 3 : 1)) k_flu
                 {
                     // W_nt from the points' normal derivatives
                     R wnt[4] = {0, 0, 0, 0};
-#pragma unroll
+#pragma unroll kSegs
                     for (int s = 0; s < 3; ++s)
 #pragma unroll
                         for (int kk = 0; kk < M; ++kk) {
