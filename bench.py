@@ -50,8 +50,8 @@ ORACLE_FLOPS = {
 # counterparts; dram__bytes_read.sum + dram__bytes_write.sum), for the
 # kernels as profiled in profiles/kernel_counters_vortex1024_o9.md: the pipe
 # utilisation beside the algorithmic rate, and the DRAM traffic per launch.
-FLUX1_EXECUTED = {"fp32": {"flops_per_cell": 20723.7, "dram_bytes_per_cell": 1422.0},
-                  "fp64": {"flops_per_cell": 21493.3, "dram_bytes_per_cell": 2751.0}}
+FLUX1_EXECUTED = {"fp32": {"flops_per_cell": 20547.6, "dram_bytes_per_cell": 1417.9},
+                  "fp64": {"flops_per_cell": 21493.3, "dram_bytes_per_cell": 2753.3}}
 
 
 def parse():
