@@ -118,13 +118,27 @@ def barrier(pg):
         pg.barrier()
 
 
-def max_over_ranks(pg, x):
-    if pg is None:
-        return x
+def _reduce(pg, x, op):
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    dev = "cuda" if pg.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(pg, x):
+    """The largest x over the ranks (this rank's x without a process group)."""
+    return x if pg is None else _reduce(pg, x, pg.ReduceOp.MAX)
+
+
+def sum_over_ranks(pg, x):
+    return x if pg is None else _reduce(pg, x, pg.ReduceOp.SUM)
+
+
+def whole_job_rate(pg, cell_stages, ms):
+    """Mcell-stage/s of the whole job: the cell-stages every rank processed
+    over the slowest rank's time (each rank passes its own count and ms)."""
+    return sum_over_ranks(pg, float(cell_stages)) / (max_over_ranks(pg, ms) / 1e3) / 1e6
 
 
 class ClockSampler:
@@ -278,9 +292,9 @@ def main():
     e2e_s = max_over_ranks(pg, time.perf_counter() - t0)
     s32.close()
 
-    value = world * cells * 2 * a.steps / (ms32 / 1e3) / 1e6
-    v64 = world * cells * 2 * k64 / (ms64 / 1e3) / 1e6
-    e2e_v = world * cells * 2 * k_e2e / e2e_s / 1e6
+    value = whole_job_rate(pg, cells * 2 * a.steps, ms32)
+    v64 = whole_job_rate(pg, cells * 2 * k64, ms64)
+    e2e_v = whole_job_rate(pg, cells * 2 * k_e2e, e2e_s * 1e3)
 
     # ---------------- measured arithmetic peaks (FMA chains on every SM)
     p32, _ = cgks.fma_peak(cgks.FP32_BULK)
