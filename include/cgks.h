@@ -262,7 +262,10 @@ const char* cgks_strerror(int code);
  * one persistent launch over a device work list of all instances, and the
  * two-stage step is one CUDA graph.  Instance k has nx[k] x ny[k] cells on
  * [ext[4k], ext[4k+1]] x [ext[4k+2], ext[4k+3]]; all share *p.  States are
- * concatenated per instance in the single-mesh layouts above. */
+ * concatenated per instance in the single-mesh layouts above.  An instance
+ * agrees with the same mesh stepped alone to rounding, not bitwise: a single
+ * mesh runs its own compilation of the stage kernels (the mesh descriptor
+ * passed by value), which may contract multiply-adds differently. */
 int cgks_batch_init(cgks_batch** out, const cgks_params* p, int n, const int* nx, const int* ny,
                     const double* ext, void* stream);
 int cgks_batch_set_state(cgks_batch* b, int k, const double* W, const double* Wx, const double* Wy,

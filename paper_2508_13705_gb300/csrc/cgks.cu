@@ -57,21 +57,22 @@ int load_tables()
             for (int b = 0; b < 12; ++b) { f[k].d1[a][b] = (float)t[k].d1[a][b]; f[k].d2[a][b] = (float)t[k].d2[a][b]; }
         }
     }
-    Kfns all[8] = {kfns_1_1_d(), kfns_1_1_f(), kfns_2_2_d(), kfns_2_3_d(), kfns_2_4_d(),
-                   kfns_2_2_f(), kfns_2_3_f(), kfns_2_4_f()};
+    // one upload per translation unit (its constant tables serve both kernel sets)
+    Kfns all[8] = {kfns_1_1_d(true), kfns_1_1_f(true), kfns_2_2_d(true), kfns_2_3_d(true), kfns_2_4_d(true),
+                   kfns_2_2_f(true), kfns_2_3_f(true), kfns_2_4_f(true)};
     for (int q = 0; q < 8; ++q)
         if (all[q].upload(t, f) != 0) return CGKS_ECUDA;
     g_tables_device = dev;
     return CGKS_OK;
 }
 
-Kfns pick_kfns(int dim, int order, int prec, int tau_mode, const int bc[4], int pt_fallback)
+Kfns pick_kfns(int dim, int order, int prec, int tau_mode, const int bc[4], int pt_fallback, bool one)
 {
     int M = (order - 1) / 2;
     Kfns k;
-    if (dim == 1) k = prec == CGKS_FP64 ? kfns_1_1_d() : kfns_1_1_f();
-    else if (prec == CGKS_FP64) k = M == 2 ? kfns_2_2_d() : (M == 3 ? kfns_2_3_d() : kfns_2_4_d());
-    else k = M == 2 ? kfns_2_2_f() : (M == 3 ? kfns_2_3_f() : kfns_2_4_f());
+    if (dim == 1) k = prec == CGKS_FP64 ? kfns_1_1_d(one) : kfns_1_1_f(one);
+    else if (prec == CGKS_FP64) k = M == 2 ? kfns_2_2_d(one) : (M == 3 ? kfns_2_3_d(one) : kfns_2_4_d(one));
+    else k = M == 2 ? kfns_2_2_f(one) : (M == 3 ? kfns_2_3_f(one) : kfns_2_4_f(one));
     // the flux instances of the mesh's collision-time mode
     if (tau_mode == CGKS_TAU_HGKS || tau_mode == CGKS_TAU_NS)
         for (int c = 0; c < 2; ++c) { k.flux1v[c] = k.flux1h[c]; k.flux2v[c] = k.flux2h[c]; }
@@ -139,6 +140,7 @@ Work work_of(const cgks_batch* b, int kind)
 {
     Work w;
     w.mesh = b->dmesh;
+    w.m0 = b->host[0];
     w.off = b->doff + (size_t)kind * (b->n + 1);
     w.n = b->n;
     w.total = b->off[(size_t)kind * (b->n + 1) + b->n];
@@ -376,7 +378,7 @@ int batch_create(cgks_batch** out, const cgks_params* p, int n, const int* nx, c
         if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) { delete b; return CGKS_ECUDA; }
         b->own_stream = true;
     }
-    b->k = pick_kfns(p->dim, p->order, p->precision, p->tau_mode, p->bc, p->pt_fallback);
+    b->k = pick_kfns(p->dim, p->order, p->precision, p->tau_mode, p->bc, p->pt_fallback, n == 1);
     std::vector<Layout> L(n);
     size_t total = 0;
     std::vector<size_t> base(n);
@@ -553,6 +555,7 @@ int launch_one(cgks_batch* b, int k, const void* fn, int kind, int arg, bool has
 {
     Work w;
     w.mesh = b->dmesh + k;
+    w.m0 = b->host[k];
     w.off = b->doff1 + ((size_t)k * W_COUNT + kind) * 2;
     w.n = 1;
     w.total = items(kind, b->dim, b->M, b->host[k].nx, b->host[k].ny);
@@ -1245,12 +1248,13 @@ extern "C" int cgks_step_1d_noalloc(const cgks_params* p, int nx, double x0, dou
     if (state_out != state_in) CK(cudaMemcpyAsync(state_out, state_in, 6 * (size_t)nx * 8, cudaMemcpyDeviceToDevice, st));
     if (sigma_in && sigma_in != sigma_out)
         CK(cudaMemcpyAsync(sigma_out, sigma_in, (size_t)(nx + 1) * 8, cudaMemcpyDeviceToDevice, st));
-    Kfns k = pick_kfns(1, p->order, p->precision, p->tau_mode, p->bc, p->pt_fallback);
+    Kfns k = pick_kfns(1, p->order, p->precision, p->tau_mode, p->bc, p->pt_fallback, true);
     int nsm = 1;
     CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
     auto go = [&](const void* fn, int kind, int stage, bool has_stage, int threads) -> int {
         Work w;
         w.mesh = dmesh;
+        w.m0 = g;
         w.off = doff + 2 * kind;
         w.n = 1;
         w.total = off[2 * kind + 1];

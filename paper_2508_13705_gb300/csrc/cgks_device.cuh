@@ -102,12 +102,16 @@ struct Mesh {
     unsigned long long* branch;     // [4] AO, r5, r7, r9 counts
 };
 
-// Prefix sums of the work items of every kernel over the meshes of a table.
+// Prefix sums of the work items of every kernel over the meshes of a table,
+// and the first mesh's descriptor by value: a launch over one mesh reads its
+// descriptor from the kernel parameters (constant-bank operands) instead of
+// loading it from the table in every grid-stride iteration.
 struct Work {
     const Mesh* mesh;
     const long long* off;  // [n+1] prefix of items
     int n;
     long long total;
+    Mesh m0;               // mesh[0]
 };
 
 __device__ __forceinline__ int find_mesh(const Work& w, long long g)
@@ -118,6 +122,17 @@ __device__ __forceinline__ int find_mesh(const Work& w, long long g)
         if (w.off[mid] <= g) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// The mesh of work item gi and the item's index within it.  ONE: the launch
+// covers a single mesh (offset 0), taken from the parameters.
+template <bool ONE>
+__device__ __forceinline__ const Mesh& mesh_of(const Work& w, long long gi, long long& local)
+{
+    if (ONE) { local = gi; return w.m0; }
+    const int k = find_mesh(w, gi);
+    local = gi - w.off[k];
+    return w.mesh[k];
 }
 
 __device__ __forceinline__ int imod(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }

@@ -233,7 +233,7 @@ __device__ __forceinline__ void step1_cell(const Mesh& g, const R* S, int dir, i
 // launched as dynamic shared memory.  Shared-memory and thread layouts keep
 // the global x index fastest.  Work items are tiles (Work offsets count
 // tiles per mesh for the tile shape of the launch).
-template <int M, typename R, bool WALLS, int DIR>
+template <int M, typename R, bool WALLS, int DIR, bool ONE>
 __global__ void __launch_bounds__(256) k_recon(Work w, int stage, int TA, int TB)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -248,12 +248,12 @@ __global__ void __launch_bounds__(256) k_recon(Work w, int stage, int TA, int TB
     R* s_dn = s_hi + (size_t)ncs * 4;               // [ncs][4] packed normal DFF (tile cells)
     const int sa = DIR == 0 ? 1 : TB;               // shared-memory stride of a
     for (long long tile = blockIdx.x; tile < w.total; tile += gridDim.x) {
-        int k = find_mesh(w, tile);
-        const Mesh& g = w.mesh[k];
+        long long ltl;
+        const Mesh& g = mesh_of<ONE>(w, tile, ltl);
         int na, nb;
         local_dims<M>(g, DIR, na, nb);
         const int nta = (na + 2 + TA - 1) / TA;
-        const int lt = (int)(tile - w.off[k]);      // 32-bit tile index (bounded on the host)
+        const int lt = (int)ltl;                    // 32-bit tile index (bounded on the host)
         const int a0 = -1 + (lt % nta) * TA, b0 = -1 + (lt / nta) * TB;
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
         const double tb = WALLS ? stage_time(g, stage) : 0.0;  // inflow ghost states
@@ -368,13 +368,14 @@ __global__ void __launch_bounds__(256) k_recon(Work w, int stage, int TA, int TB
         }
         __syncthreads();  // the next tile reuses the shared memory
     }
-    if (threadIdx.x < 4 && cnt[threadIdx.x] && w.n > 0) atomicAdd(&w.mesh[0].branch[threadIdx.x], cnt[threadIdx.x]);
+    if (threadIdx.x < 4 && cnt[threadIdx.x] && w.n > 0)
+        atomicAdd(&(ONE ? w.m0 : w.mesh[0]).branch[threadIdx.x], cnt[threadIdx.x]);
 }
 
 // -------------------------------------------------------------- Step 2 (1-D)
 // The reconstruction of a 1-D cell a in [-1, nx] from the cell averages and
 // slopes of a-2..a+2: the right state of face a and the left state of face a+1.
-template <typename R, bool WALLS>
+template <typename R, bool WALLS, bool ONE>
 __global__ void __launch_bounds__(256) k_normal1(Work w, int stage)
 {
     __shared__ unsigned long long cnt[4];
@@ -384,9 +385,9 @@ __global__ void __launch_bounds__(256) k_normal1(Work w, int stage)
     constexpr bool BULK32 = sizeof(R) == 4;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
          gi += (long long)gridDim.x * blockDim.x) {
-        int k = find_mesh(w, gi);
-        const Mesh& g = w.mesh[k];
-        const int a = (int)(gi - w.off[k]) - 1;
+        long long li;
+        const Mesh& g = mesh_of<ONE>(w, gi, li);
+        const int a = (int)li - 1;
         const int na = g.nx;
         const R* S = state_planes<R>(g, stage == 1 ? 0 : 1);
         const double tb = WALLS ? stage_time(g, stage) : 0.0;  // inflow ghost states
@@ -447,7 +448,8 @@ __global__ void __launch_bounds__(256) k_normal1(Work w, int stage)
         }
     }
     __syncthreads();
-    if (threadIdx.x < 4 && cnt[threadIdx.x] && w.n > 0) atomicAdd(&w.mesh[0].branch[threadIdx.x], cnt[threadIdx.x]);
+    if (threadIdx.x < 4 && cnt[threadIdx.x] && w.n > 0)
+        atomicAdd(&(ONE ? w.m0 : w.mesh[0]).branch[threadIdx.x], cnt[threadIdx.x]);
 }
 
 // -------------------------------------------------------------- Step 3 + flux
@@ -464,7 +466,7 @@ __global__ void __launch_bounds__(256) k_normal1(Work w, int stage)
 // collision-time terms (tau > 0); the tau = 0 instance leaves them out and
 // carries fewer live values.  PF = true compiles the first-order fallback at
 // face points whose reconstructed state is not physical (a flagged option).
-template <int D, int M, typename R, int STAGE, int CAP, int HG, bool PF = false>
+template <int D, int M, typename R, int STAGE, int CAP, int HG, bool PF, bool ONE>
 __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? (HG ? 3 : 4) : 1)) k_flux(Work w)
 {
     constexpr int NV = D + 2;
@@ -482,7 +484,7 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? (HG ? 3 : 4) 
     __shared__ R s_d1[4][12], s_d2[4][12];
     __shared__ R s_c1[4][3], s_c2[4][3];
     if (D == 2) {
-        const auto& T = Tab<R>::get(w.mesh[0].oi);  // a table shares one order
+        const auto& T = Tab<R>::get((ONE ? w.m0 : w.mesh[0]).oi);  // a table shares one order
         for (int q = threadIdx.x; q < 48; q += blockDim.x) {
             s_d1[q / 12][q % 12] = T.d1[q / 12][q % 12];
             s_d2[q / 12][q % 12] = T.d2[q / 12][q % 12];
@@ -498,9 +500,9 @@ __global__ void __launch_bounds__(128, CAP ? 4 : (sizeof(R) == 4 ? (HG ? 3 : 4) 
     }
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
          gi += (long long)gridDim.x * blockDim.x) {
-        int k = find_mesh(w, gi);
-        const Mesh& g = w.mesh[k];
-        unsigned li = (unsigned)(gi - w.off[k]);  // 32-bit local index (bounded on the host)
+        long long lil;
+        const Mesh& g = mesh_of<ONE>(w, gi, lil);
+        unsigned li = (unsigned)lil;  // 32-bit local index (bounded on the host)
         int dir = 0, na = g.nx, nb = 1;
         if (D == 2) {
             unsigned nxl = (unsigned)(g.nx + 1) * (unsigned)g.ny * M;
@@ -915,15 +917,14 @@ __device__ __forceinline__ double exact_diff(float r, float l)
 // Stage 1 writes W* (S1) and the accumulator; stage 2 writes state n+1 (S0).
 // FP32-bulk form: the float planes (F1 / F0) receive everything the next stage
 // reads, the FP64 planes the cell averages of state n+1 (W* lives in F1 only).
-template <int M, typename R, int STAGE>
+template <int M, typename R, int STAGE, bool ONE>
 __global__ void __launch_bounds__(256) k_update2(Work w)
 {
     constexpr bool BULK32 = sizeof(R) == 4;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
          gi += (long long)gridDim.x * blockDim.x) {
-        int k = find_mesh(w, gi);
-        const Mesh& g = w.mesh[k];
-        long long c = gi - w.off[k];
+        long long c;
+        const Mesh& g = mesh_of<ONE>(w, gi, c);
         unsigned cu = (unsigned)c, qj = cu / (unsigned)g.nx;  // 32-bit (bounded on the host)
         int i = (int)(cu - qj * (unsigned)g.nx), j = (int)qj;
         const R* FX = (const R*)g.FO[0];
@@ -1110,15 +1111,15 @@ __global__ void __launch_bounds__(256) k_update2(Work w)
 }
 
 // -------------------------------------------------------------- update (1-D)
-template <typename R, int STAGE>
+template <typename R, int STAGE, bool ONE>
 __global__ void __launch_bounds__(256) k_update1(Work w)
 {
     constexpr bool BULK32 = sizeof(R) == 4;
     for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < w.total;
          gi += (long long)gridDim.x * blockDim.x) {
-        int k = find_mesh(w, gi);
-        const Mesh& g = w.mesh[k];
-        int i = (int)(gi - w.off[k]);
+        long long il;
+        const Mesh& g = mesh_of<ONE>(w, gi, il);
+        int i = (int)il;
         const R* FX = (const R*)g.FO[0];
         // q-th output quantity of variable v at face i (left) or i + 1 (right)
         const long long nf = g.nx + 1;

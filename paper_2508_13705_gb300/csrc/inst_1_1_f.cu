@@ -1,5 +1,5 @@
 // Kernels of the 1-D configuration with 1 Gauss point(s) per face in float.
 #include "kfns_impl.cuh"
 namespace cgks {
-Kfns kfns_1_1_f() { return make_kfns<1, 1, float>(); }
+Kfns kfns_1_1_f(bool one) { return make_kfns<1, 1, float>(one); }
 }

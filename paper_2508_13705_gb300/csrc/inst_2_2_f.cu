@@ -1,5 +1,5 @@
 // Kernels of the 2-D configuration with 2 Gauss point(s) per face in float.
 #include "kfns_impl.cuh"
 namespace cgks {
-Kfns kfns_2_2_f() { return make_kfns<2, 2, float>(); }
+Kfns kfns_2_2_f(bool one) { return make_kfns<2, 2, float>(one); }
 }

@@ -1,5 +1,5 @@
 // Kernels of the 2-D configuration with 3 Gauss point(s) per face in double.
 #include "kfns_impl.cuh"
 namespace cgks {
-Kfns kfns_2_3_d() { return make_kfns<2, 3, double>(); }
+Kfns kfns_2_3_d(bool one) { return make_kfns<2, 3, double>(one); }
 }

@@ -1,5 +1,6 @@
 // Kernel entry points of one (dimension, Gauss points, precision)
 // configuration; each configuration is compiled in its own translation unit.
+// one: the stage kernels for launches over a single mesh.
 #pragma once
 #include "cgks_device.cuh"
 
@@ -18,12 +19,12 @@ struct Kfns {
     KOne flux1p, flux2p;        // tau > 0 with the first-order fallback at face points
     int (*upload)(const CgksTables* t3, const TabF* f3);  // constant tables of this unit
 };
-Kfns kfns_1_1_d();
-Kfns kfns_1_1_f();
-Kfns kfns_2_2_d();
-Kfns kfns_2_3_d();
-Kfns kfns_2_4_d();
-Kfns kfns_2_2_f();
-Kfns kfns_2_3_f();
-Kfns kfns_2_4_f();
+Kfns kfns_1_1_d(bool one);
+Kfns kfns_1_1_f(bool one);
+Kfns kfns_2_2_d(bool one);
+Kfns kfns_2_3_d(bool one);
+Kfns kfns_2_4_d(bool one);
+Kfns kfns_2_2_f(bool one);
+Kfns kfns_2_3_f(bool one);
+Kfns kfns_2_4_f(bool one);
 }
