@@ -50,8 +50,8 @@ ORACLE_FLOPS = {
 # counterparts; dram__bytes_read.sum + dram__bytes_write.sum), for the
 # kernels as profiled in profiles/kernel_counters_vortex1024_o9.md: the pipe
 # utilisation beside the algorithmic rate, and the DRAM traffic per launch.
-FLUX1_EXECUTED = {"fp32": {"flops_per_cell": 20547.6, "dram_bytes_per_cell": 1417.9},
-                  "fp64": {"flops_per_cell": 21493.3, "dram_bytes_per_cell": 2753.3}}
+FLUX1_EXECUTED = {"fp32": {"flops_per_cell": 20723.8, "dram_bytes_per_cell": 1417.5},
+                  "fp64": {"flops_per_cell": 21389.3, "dram_bytes_per_cell": 2711.5}}
 
 
 def parse():
