@@ -85,6 +85,29 @@ def test_vortex_2048_order9_sampled_parity_fp64_and_fp32():
     check(results[cgks.FP32_BULK][1], samples, 1e-6, 10.0 / n, fields=("W",))
 
 
+def test_vortex_1024_order9_autotuned_sampled_parity():
+    """The bench's headline workload and launch shapes: 1024^2, autotuned
+    (tile shapes and block sizes), one graph step with the device CFL step."""
+    n, order = 1024, 9
+    ext = (0.0, 10.0, 0.0, 10.0)
+    st = inputs.vortex_2d(n, order)
+    results = {}
+    for prec in (cgks.FP64, cgks.FP32_BULK):
+        s = cgks.Solver(2, order, n, n, extent=ext, precision=prec)
+        s.set_state(*st)
+        s.autotune()
+        dt = s.compute_dt()
+        s.advance(1, 0.0)
+        t, rc, _ = s.sync()
+        assert rc == 0 and abs(t - dt) < 1e-15
+        results[prec] = (dt, s.get_state())
+        s.close()
+    dt = results[cgks.FP64][0]
+    samples = sampled_oracle(st, ext, n, order, dt, [(512, 512), (300, 700), (3, 1020)])
+    check(results[cgks.FP64][1], samples, 1e-12, 10.0 / n)
+    check(results[cgks.FP32_BULK][1], samples, 1e-6, 10.0 / n, fields=("W",))
+
+
 def test_quadrants_4096_order9_fp32_sampled():
     """Config C4 at full size (4096^2, FP32 bulk, transmissive, HGKS tau):
     two graph steps; samples near the quadrant corner and on a shock line."""
