@@ -149,6 +149,28 @@ def test_density_wave_2d_multi_step(order):
     compare(s.get_state(), o, FIELDS_2D, what="2-D wave order %d" % order)
 
 
+@pytest.mark.parametrize("precision", [cgks.FP64, cgks.FP32_BULK])
+@pytest.mark.parametrize("order", [5, 9])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (2, 3), (5, 1), (1, 7), (3, 4)])
+def test_tiny_periodic_meshes(nx, ny, order, precision):
+    """Degenerate sizes: fewer cells than a stencil spans, so every stencil
+    wraps around the mesh more than once (a single cell sees only itself).
+    Two steps of an oblique density wave against the oracle.  FP32 bulk: the
+    increments here are as large as the wave's amplitude (0.2 across one
+    cell), so its rounding bound is 2^-24 x 0.2 per operation, about 1e-8
+    relative; the bound allows 1e-7."""
+    def prim(x, y):
+        return 1 + 0.2 * np.sin(2 * np.pi * (x + 2 * y)), 0.5 + 0 * x, -0.3 + 0 * x, 1 + 0 * x
+    st = inputs.cell_state_2d(prim, nx, ny, (0, 1, 0, 1), order)
+    s, o = run_both(2, order, nx, st, 2, (0, 1, 0, 1), ny=ny, precision=precision)
+    t, rc, _ = s.sync()
+    assert rc == 0 and o.flags == 0
+    if precision == cgks.FP64:
+        compare(s.get_state(), o, FIELDS_2D, what="%dx%d order %d" % (nx, ny, order))
+    else:
+        compare(s.get_state(), o, ("W",), tol=1e-7, what="%dx%d order %d FP32" % (nx, ny, order))
+
+
 @pytest.mark.parametrize("order", [7, 9])
 def test_vortex_ragged_mesh(order):
     """Isentropic vortex (config C3 shape) on a ragged nx != ny mesh."""
