@@ -93,6 +93,37 @@ def test_batch_instance_matches_oracle():
             assert d <= 1e-12 * np.abs(ref).sum() + ref.size * floor, (k, f, d)
 
 
+def test_batch_with_degenerate_instances_matches_oracle():
+    """Instances smaller than a stencil (1 x 1, 2 x 3, 5 x 1) beside an
+    ordinary one in one batch: the descriptor table, the work lists and the
+    periodic wrap of each, against the oracle per instance."""
+    order = 9
+    dims = [(1, 1), (2, 3), (5, 1), (17, 9)]
+
+    def prim(x, y):
+        return 1 + 0.2 * np.sin(2 * np.pi * (x + 2 * y)), 0.5 + 0 * x, -0.3 + 0 * x, 1 + 0 * x
+    ext = (0.0, 1.0, 0.0, 1.0)
+    states = [inputs.cell_state_2d(prim, nx, ny, ext, order) for nx, ny in dims]
+    b = cgks.Batch(order, [d[0] for d in dims], [d[1] for d in dims], [ext] * len(dims))
+    for k, st in enumerate(states):
+        b.set_state(k, *st)
+    dts = np.array([1e-3 * (1 + 0.5 * k) for k in range(len(dims))])
+    for _ in range(2):
+        b.step(dts)
+    b.sync()
+    for k, ((nx, ny), st) in enumerate(zip(dims, states)):
+        o = oracle.Oracle(2, order, nx, ny, extent=ext)
+        o.set_state(*st)
+        o.step(dts[k])
+        o.step(dts[k])
+        g = b.get_state(k)
+        assert np.abs(g["W"] - o.W).sum() <= 1e-12 * np.abs(o.W).sum(), k
+        floor = 64 * np.finfo(float).eps * np.abs(o.W).max() / min(o.dx, o.dy)
+        for f, ref in (("Wx_line", o.Wxl), ("Wy_line", o.Wyl)):
+            d = np.abs(g[f] - ref).sum()
+            assert d <= 1e-12 * np.abs(ref).sum() + ref.size * floor, (k, f, d)
+
+
 def test_batch_device_state_calls_equal_host_calls():
     """cgks_batch_set_state_device / _get_state_device (CUDA tensors, enqueued
     on the batch's stream) give bitwise the same steps as the host-array calls,

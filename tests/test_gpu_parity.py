@@ -99,6 +99,22 @@ def test_density_wave_1d_full_run(order):
     compare(s.get_state(), o, FIELDS_1D, what="1-D order %d" % order)
 
 
+@pytest.mark.parametrize("precision", [cgks.FP64, cgks.FP32_BULK])
+@pytest.mark.parametrize("order", [5, 9])
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_tiny_periodic_meshes_1d(N, order, precision):
+    """1-D meshes of fewer cells than a stencil spans (the wrap reaches the
+    same cells several times), two CFL steps of the density wave against the
+    oracle; FP32 bound as for the 2-D tiny meshes."""
+    s, o = run_both(1, order, N, inputs.density_wave_1d(N), 2, (0, 2, 0, 1), precision=precision)
+    t, rc, _ = s.sync()
+    assert rc == 0 and o.flags == 0
+    if precision == cgks.FP64:
+        compare(s.get_state(), o, FIELDS_1D, what="1-D N=%d order %d" % (N, order))
+    else:
+        compare(s.get_state(), o, ("W",), tol=1e-7, what="1-D N=%d order %d FP32" % (N, order))
+
+
 @pytest.mark.parametrize("order", [5, 9])
 def test_sod_1d_per_step(order):
     """Shock tube: every step starts both from the oracle's state; the DFF
