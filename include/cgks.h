@@ -45,7 +45,8 @@ extern "C" {
 #define CGKS_ENOMEM (-2)     /* device allocation failed */
 #define CGKS_ECUDA (-3)      /* a CUDA runtime call failed */
 #define CGKS_ENONPHYS (-4)   /* non-positive density / pressure or non-finite value */
-#define CGKS_ETIMEOUT (-5)   /* a bounded device wait gave up */
+#define CGKS_ETIMEOUT (-5)   /* reserved: a bounded device wait gave up (no kernel here waits on
+                                another block or launch, so none is returned) */
 #define CGKS_ENOTSUP (-6)    /* combination of options not supported */
 
 /* precision of the reconstruction and kinetic arithmetic */

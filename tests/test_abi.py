@@ -49,6 +49,30 @@ def test_invalid_parameters_rejected_without_gpu(L):
     assert cgks.strerror(cgks.ENONPHYS).startswith("non-positive")
 
 
+def test_size_limits_rejected_without_gpu(L):
+    """Host-side limits, checked before any device call: a wall needs three
+    cells to mirror its ghost layers onto; a mesh's work items are indexed in
+    32 bits (2-D order 9 has 8 (n + 1) n face points at n x n); the point
+    fallback is compiled into the tau > 0 flux only."""
+    import ctypes
+    h = ctypes.c_void_p()
+    for bc, nx, ny in (((cgks.BC_REFLECTIVE, 0, 0, 0), 2, 8), ((0, 0, cgks.BC_NOSLIP, 0), 8, 2)):
+        p = cgks.make_params(2, 9)
+        for k in range(4):
+            p.bc[k] = bc[k]
+        assert L.cgks_init_mesh(ctypes.byref(h), ctypes.byref(p), nx, ny, 0.0, 1.0, 0.0, 1.0, None) == cgks.EINVAL
+        assert not h.value
+    n = 16385  # 8 * 16386 * 16385 >= 2^31 face points
+    p = cgks.make_params(2, 9)
+    assert 8 * (n + 1) * n >= 2 ** 31
+    assert L.cgks_init_mesh(ctypes.byref(h), ctypes.byref(p), n, n, 0.0, 1.0, 0.0, 1.0, None) == cgks.EINVAL
+    assert not h.value
+    p = cgks.make_params(2, 9)
+    p.pt_fallback = cgks.PT_FALLBACK_FIRST_ORDER  # with the default tau = 0
+    assert L.cgks_init_mesh(ctypes.byref(h), ctypes.byref(p), 8, 8, 0.0, 1.0, 0.0, 1.0, None) == cgks.ENOTSUP
+    assert not h.value
+
+
 GOLD = os.path.join(ROOT, "tests", "golden", "stencils_eq3_8_3_10_3_18.txt")
 ST = {"S0": 0, "S1": 1, "S2": 2, "r5": 3, "r7": 4, "r9": 5}
 
